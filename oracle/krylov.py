@@ -1,0 +1,124 @@
+"""Arnoldi on g_k(U), Rayleigh quotients, residuals and target selection: CPU oracle
+(test infrastructure; see ``oracle/__init__``).
+
+Sec. 4 builds an orthonormal Krylov basis V of g_k(U) from a random start vector,
+projects g_k(U) to the upper Hessenberg H_m = V^H g_k(U) V (Eq. arnoldi), takes Ritz pairs
+of H_m, and then recovers the eigenvalue of U from the Ritz vector |n> by the Rayleigh
+quotient omega_n = <n|U|n> together with the residual r_n = ||U|n> - omega_n |n>||_2
+(Eq. residual). The paper runs ARPACK's implicitly restarted Arnoldi; ``arpack_eigs`` does
+the same through scipy. The plain definition of the result (Sec. 3: all nev eigenpairs of
+U with eigenvalues nearest the target on the unit circle) is ``dense_eigs``.
+
+Readings taken where the paper is silent:
+  * "closest" = smallest wrapped angle |arg(omega exp(-i phi))|; ties by ascending arg;
+  * the eigenvalue is the Rayleigh quotient itself, not projected onto |omega| = 1;
+  * Gram-Schmidt is classical with one full reorthogonalisation (CGS2).
+
+Parity: ``arnoldi`` is pinned by V^H V = I and g_k(U) V_m = V_{m+1} H_m; ``dense_eigs`` by
+unitarity and the closed-form spectra of the special cases; ``arpack_eigs`` against
+``dense_eigs`` (tests/test_oracle.py).
+"""
+
+import numpy as np
+
+from . import geosum
+
+
+def cgs2(V, w):
+    """Orthogonalise w against the orthonormal columns of V by classical Gram-Schmidt,
+    twice. Returns (h, beta, q): V^H-coefficients summed over both passes, ||w_perp||,
+    and the unit vector w_perp / beta."""
+    h1 = V.conj().T @ w
+    w = w - V @ h1
+    h2 = V.conj().T @ w
+    w = w - V @ h2
+    beta = np.linalg.norm(w)
+    return h1 + h2, beta, w / beta
+
+
+def arnoldi(apply_op, v0, m):
+    """m Arnoldi steps from v0 (Eq. arnoldi): V (d x (m+1)) orthonormal, H ((m+1) x m)
+    upper Hessenberg with apply_op(V[:, :m]) = V @ H."""
+    d = v0.shape[0]
+    V = np.zeros((d, m + 1), dtype=np.complex128)
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    V[:, 0] = v0 / np.linalg.norm(v0)
+    for j in range(m):
+        w = apply_op(V[:, j])
+        h, beta, q = cgs2(V[:, : j + 1], w)
+        H[: j + 1, j] = h
+        H[j + 1, j] = beta
+        V[:, j + 1] = q
+    return V, H
+
+
+def rayleigh_residual(op, X):
+    """For each column x (normalised here): omega = <x|U|x>, r = ||U x - omega x||_2."""
+    n = X.shape[1]
+    omega = np.empty(n, dtype=np.complex128)
+    resid = np.empty(n, dtype=np.float64)
+    Xn = X / np.linalg.norm(X, axis=0, keepdims=True)
+    for i in range(n):
+        x = Xn[:, i]
+        ux = op.apply_u(x)
+        omega[i] = np.vdot(x, ux)
+        resid[i] = np.linalg.norm(ux - omega[i] * x)
+    return omega, resid, Xn
+
+
+def angular_distance(omega, phi):
+    """|arg(omega exp(-i phi))| in [0, pi]."""
+    return np.abs(np.angle(np.asarray(omega) * np.exp(-1j * phi)))
+
+
+def select_closest(omega, phi, nev):
+    """Indices of the nev values closest to exp(i phi) by wrapped angle, ties broken by
+    ascending arg(omega exp(-i phi))."""
+    rel = np.angle(np.asarray(omega) * np.exp(-1j * phi))
+    order = np.lexsort((rel, np.abs(rel)))
+    return order[:nev]
+
+
+def dense_eigs(op, phi, nev):
+    """The plain definition: all eigenpairs of dense U (LAPACK zgeev via scipy), the nev
+    closest to exp(i phi). Returns (omega, vectors d x nev, residuals)."""
+    from scipy.linalg import eig
+
+    U = op.dense()
+    w, v = eig(U)
+    idx = select_closest(w, phi, nev)
+    omega, resid, Xn = rayleigh_residual(op, v[:, idx])
+    return omega, Xn, resid
+
+
+def arpack_eigs(op, phi, k, nev, m, v0, tol=1e-13, max_req=None):
+    """Sec. 4 route: ARPACK ('LM') on g_k(U), then omega = <n|U|n> and r_n.
+
+    ARPACK ranks Ritz values by |g_k|, which orders eigenvalues by closeness only inside
+    the main lobe |x| < 2 pi / k. The number of requested pairs n_req is therefore grown
+    until the nev-th closest in-lobe eigenvalue has a strictly larger |g_k| than the
+    smallest converged Ritz value: every eigenvalue closer than the nev-th one has a
+    larger |g_k| still (|g_k| falls monotonically across the lobe), so it lies above the
+    cut and is among the n_req converged.
+    """
+    from scipy.sparse.linalg import LinearOperator, eigs
+
+    d = op.d
+    A = LinearOperator((d, d), matvec=lambda x: geosum.filter_acc(op, x.ravel(), phi, k),
+                       dtype=np.complex128)
+    n_req = nev + max(2, nev // 4)
+    max_req = max_req or (m - 2)
+    while True:
+        n_req = min(n_req, max_req)
+        theta, X = eigs(A, k=n_req, ncv=m, which="LM", v0=v0, tol=tol, maxiter=10000)
+        omega, resid, Xn = rayleigh_residual(op, X)
+        inlobe = angular_distance(omega, phi) < 2 * np.pi / k
+        idx = select_closest(omega[inlobe], phi, nev)
+        cand = np.flatnonzero(inlobe)[idx]
+        if len(cand) == nev:
+            g_nev = np.abs(geosum.gk_closed(omega[cand[-1:]], phi, k))[0]
+            if g_nev > np.abs(theta).min() * (1 + 1e-9):
+                return omega[cand], Xn[:, cand], resid[cand]
+        if n_req == max_req:
+            raise RuntimeError("ARPACK route could not isolate nev in-lobe eigenvalues")
+        n_req = n_req + max(4, nev // 2)

@@ -1,0 +1,351 @@
+"""Pins of the CPU oracle against quantities fixed independently of it.
+
+Each test checks the oracle against something it does not compute itself: dense matrix
+exponentials of Kronecker-product generators, brute-force loops on tiny inputs, closed-form
+spectra of special cases, the paper's statements about g_k (tests/golden), unitarity and
+exact algebraic identities. The ``planted`` tests put a plausible mistake into the oracle
+(on the CPU) and check that one of these pins catches it.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import geosum, krylov, model
+from paper_2102_05054_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sorted_on_circle(w):
+    w = np.asarray(w)
+    return w[np.lexsort((np.abs(w), np.angle(w)))]
+
+
+def _same_multiset_on_circle(a, b, tol):
+    """Every value of a has a partner in b within tol (bipartite by greedy nearest)."""
+    a = list(np.asarray(a))
+    b = list(np.asarray(b))
+    assert len(a) == len(b)
+    bb = np.array(b)
+    used = np.zeros(len(bb), dtype=bool)
+    for x in a:
+        dist = np.abs(bb - x)
+        dist[used] = np.inf
+        j = int(np.argmin(dist))
+        assert dist[j] <= tol, (x, dist[j])
+        used[j] = True
+
+
+# ---------------------------------------------------------------- model: U = D K
+
+
+@pytest.mark.parametrize("L", [3, 4, 5])
+def test_phases_brute_force(L):
+    rng = np.random.default_rng(7 + L)
+    J = 0.7
+    h = rng.uniform(-1, 1, L)
+    theta = model.diagonal_phases(L, J, h)
+    for s in range(1 << L):
+        zs = [1 if ((s >> i) & 1) == 0 else -1 for i in range(L)]
+        want = 0.0
+        for i in range(L):
+            want += J * zs[i] * zs[(i + 1) % L] + h[i] * zs[i]
+        assert abs(theta[s] - want) < 1e-13
+
+
+@pytest.mark.parametrize("L,J,g", [(3, 1.0, 0.9045), (4, 0.3, 0.2), (5, 1.0, 1.3),
+                                   (6, -0.8, 0.9045), (7, 1.0, 2.5)])
+def test_apply_u_matches_dense_expm(L, J, g):
+    h = inputs.disorder(L, 1.5, 100 + L)
+    op = model.KickedIsing(L, J, g, h)
+    U_ref = model.dense_u_expm(L, J, g, h)
+    assert np.abs(op.dense() - U_ref).max() < 1e-13
+
+
+def test_unitarity_dense():
+    L = 8
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 3))
+    U = op.dense()
+    assert np.abs(U.conj().T @ U - np.eye(1 << L)).max() < 1e-13
+
+
+def test_norm_preserved_L14():
+    L = 14
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 4))
+    psi = inputs.complex_gaussian(1 << L, 9)
+    for _ in range(5):
+        psi = op.apply_u(psi)
+    assert abs(np.linalg.norm(psi) - 1.0) < 1e-13
+
+
+def test_special_case_g0_any_L():
+    # g = 0: U = D, eigenpairs (exp(-i theta_s), |s>) in closed form, checked at L = 16.
+    L = 16
+    h = inputs.disorder(L, 2.0, 5)
+    op = model.KickedIsing(L, 1.0, 0.0, h)
+    lam = model.spectrum_g0(L, 1.0, h)
+    rng = np.random.default_rng(0)
+    for s in rng.integers(0, 1 << L, 20):
+        e = np.zeros(1 << L, dtype=np.complex128)
+        e[s] = 1.0
+        u = op.apply_u(e)
+        assert abs(u[s] - lam[s]) < 1e-14
+        u[s] = 0
+        assert np.abs(u).max() < 1e-14
+
+
+def test_special_case_g0_dense_spectrum():
+    L = 7
+    h = inputs.disorder(L, 1.0, 6)
+    op = model.KickedIsing(L, 1.0, 0.0, h)
+    _same_multiset_on_circle(np.linalg.eigvals(op.dense()), model.spectrum_g0(L, 1.0, h), 1e-12)
+
+
+def test_special_case_j0_spectrum():
+    L = 7
+    h = inputs.disorder(L, 1.0, 8)
+    op = model.KickedIsing(L, 0.0, 0.9045, h)
+    _same_multiset_on_circle(np.linalg.eigvals(op.dense()), model.spectrum_j0(L, 0.9045, h),
+                             1e-11)
+
+
+@pytest.mark.parametrize("L", [6, 7])
+def test_special_case_g_half_pi_spectrum(L):
+    h = inputs.disorder(L, 1.0, 9)
+    op = model.KickedIsing(L, 1.0, math.pi / 2, h)
+    _same_multiset_on_circle(np.linalg.eigvals(op.dense()),
+                             model.spectrum_g_half_pi(L, 1.0, h), 1e-11)
+
+
+# ---------------------------------------------------------------- filter g_k(U)
+
+
+def _paper_facts():
+    facts = {}
+    with open(os.path.join(GOLDEN, "paper_gk_facts.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, value, _cite = [x.strip() for x in line.split("|")]
+            facts[name] = value
+    return facts
+
+
+@pytest.mark.parametrize("k", [2, 7, 30, 64, 1024])
+def test_gk_paper_facts(k):
+    facts = _paper_facts()
+    n_terms = k
+    phi = 0.37
+    peak = eval(facts["peak_modulus"], {"n_terms": n_terms})
+    zero = eval(facts["first_zero_offset"], {"n_terms": n_terms, "pi": math.pi})
+    assert abs(geosum.gk_closed(np.exp(1j * phi), phi, k)[0] - peak) < 1e-12
+    # closed form of the paper against direct summation of the series
+    x = np.linspace(-math.pi, math.pi, 41) + 1e-3
+    w = np.exp(1j * x)
+    direct = sum(w ** j for j in range(k))
+    paper = eval(facts["closed_form"], {"n_terms": n_terms, "w": w})
+    assert np.abs(paper - direct).max() < 1e-9 * k
+    assert np.abs(geosum.gk_closed(np.exp(1j * (x + phi)), phi, k) - direct).max() < 1e-9 * k
+    # zeros at +-2 pi / k, and |g| falls monotonically across the main lobe
+    for sgn in (+1, -1):
+        assert abs(geosum.gk_closed(np.exp(1j * (phi + sgn * zero)), phi, k)[0]) < 1e-9 * k
+    t = np.linspace(0, zero, 200)
+    mod = geosum.gk_on_circle(phi + t, phi, k)
+    assert np.all(np.diff(mod) <= 1e-9 * k)
+    # the sine-ratio form agrees with the closed form
+    assert np.allclose(mod, np.abs(geosum.gk_closed(np.exp(1j * (phi + t)), phi, k)),
+                       atol=1e-9 * k)
+
+
+def test_lobe_count_statistics():
+    # 2d/k eigenvalues on the outer lobe on average (Sec. 3); across targets the mean count
+    # over 16 targets must be close to 2d/k.
+    L, k = 10, 32
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 11))
+    ev = np.linalg.eigvals(op.dense())
+    counts = [np.sum(krylov.angular_distance(ev, phi) < 2 * math.pi / k)
+              for phi in np.linspace(0, 2 * math.pi, 16, endpoint=False)]
+    expect = eval(_paper_facts()["lobe_count"], {"d": 1 << L, "n_terms": k})
+    assert abs(np.mean(counts) - expect) < 0.15 * expect
+
+
+def test_filter_closed_form_on_exact_eigenvectors():
+    L, k, phi = 8, 37, 0.4
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 12))
+    w, v = np.linalg.eig(op.dense())
+    for i in range(0, 1 << L, 17):
+        out = geosum.filter_acc(op, v[:, i], phi, k)
+        want = geosum.gk_closed(w[i:i + 1], phi, k)[0] * v[:, i]
+        assert np.abs(out - want).max() < 1e-11 * k
+
+
+def test_filter_peaks_at_target_eigenvalue():
+    # Sec. 3: the phase factor rotates the target to 1, where |g_k| peaks at the number of
+    # terms. Choose phi = arg(omega) for an exact eigenvalue: g_k(U) v = k v.
+    L, k = 7, 23
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 23))
+    w, v = np.linalg.eig(op.dense())
+    for i in (0, 5, 40):
+        phi = float(np.angle(w[i]))
+        out = geosum.filter_acc(op, v[:, i], phi, k)
+        assert np.abs(out - k * v[:, i]).max() < 1e-11 * k
+        out = geosum.filter_horner(op, v[:, i], phi, k)
+        assert np.abs(out - k * v[:, i]).max() < 1e-11 * k
+
+
+def test_filter_forms_agree_with_dense_definition():
+    L, k, phi = 6, 11, 1.1
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 13))
+    psi = inputs.complex_gaussian(1 << L, 14)
+    G = geosum.filter_dense(op.dense(), phi, k)
+    a = geosum.filter_acc(op, psi, phi, k)
+    b = geosum.filter_horner(op, psi, phi, k)
+    assert np.abs(a - G @ psi).max() < 1e-12
+    assert np.abs(b - G @ psi).max() < 1e-12
+
+
+def test_filter_telescoping_identity():
+    # (1 - z U) g_k(U) psi = psi - z^k U^k psi
+    L, k, phi = 12, 50, math.pi / 3
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 2.0, 15))
+    psi = inputs.complex_gaussian(1 << L, 16)
+    acc = geosum.filter_acc(op, psi, phi, k)
+    lhs = acc - geosum.zpow(phi, 1) * op.apply_u(acc)
+    uk = psi.copy()
+    for _ in range(k):
+        uk = op.apply_u(uk)
+    rhs = psi - geosum.zpow(phi, k) * uk
+    assert np.abs(lhs - rhs).max() < 1e-12
+
+
+def test_filter_commutes_with_u():
+    L, k, phi = 10, 20, 0.9
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 17))
+    psi = inputs.complex_gaussian(1 << L, 18)
+    a = op.apply_u(geosum.filter_acc(op, psi, phi, k))
+    b = geosum.filter_acc(op, op.apply_u(psi), phi, k)
+    assert np.abs(a - b).max() < 1e-12
+
+
+# ---------------------------------------------------------------- Arnoldi and eigenpairs
+
+
+def test_arnoldi_relation():
+    L, k, phi, m = 8, 16, 0.0, 24
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 19))
+    v0 = inputs.complex_gaussian(1 << L, 20)
+    A = lambda x: geosum.filter_acc(op, x, phi, k)  # noqa: E731
+    V, H = krylov.arnoldi(A, v0, m)
+    assert np.abs(V.conj().T @ V - np.eye(m + 1)).max() < 1e-13
+    AV = np.stack([A(V[:, j]) for j in range(m)], axis=1)
+    assert np.abs(AV - V @ H).max() < 1e-12 * np.abs(H).max()
+    assert np.abs(np.tril(H, -2)).max() == 0.0
+    # H_m equals the projection V^H g_k(U) V (Eq. arnoldi)
+    assert np.abs(V[:, :m].conj().T @ AV - H[:m]).max() < 1e-12 * np.abs(H).max()
+
+
+def test_select_closest_brute_force():
+    rng = np.random.default_rng(21)
+    ang = rng.uniform(-math.pi, math.pi, 50)
+    omega = np.exp(1j * ang)
+    phi = 2.5
+    idx = krylov.select_closest(omega, phi, 7)
+    dist = [abs((a - phi + math.pi) % (2 * math.pi) - math.pi) for a in ang]
+    want = sorted(range(50), key=lambda i: dist[i])[:7]
+    assert list(idx) == want
+
+
+def test_dense_eigs_special_case_g0():
+    L, phi, nev = 8, 1.0, 12
+    h = inputs.disorder(L, 1.0, 22)
+    op = model.KickedIsing(L, 1.0, 0.0, h)
+    om, X, r = krylov.dense_eigs(op, phi, nev)
+    lam = model.spectrum_g0(L, 1.0, h)
+    want = lam[krylov.select_closest(lam, phi, nev)]
+    assert np.abs(om - want).max() < 1e-13
+    assert r.max() < 1e-13
+
+
+@pytest.mark.slow
+def test_arpack_route_matches_dense_L10():
+    cfg = inputs.WORKLOADS["kicked_ising_L10"]
+    L = cfg["L"]
+    op = model.KickedIsing(L, inputs.J_DEFAULT, inputs.G_DEFAULT,
+                           inputs.disorder(L, cfg["W"], cfg["seed"]))
+    om_d, X_d, r_d = krylov.dense_eigs(op, cfg["phi"], cfg["nev"])
+    om_a, X_a, r_a = krylov.arpack_eigs(op, cfg["phi"], cfg["k"], cfg["nev"], cfg["m"],
+                                        inputs.start_vector(L))
+    assert np.abs(om_d - om_a).max() < 1e-10
+    ov = np.abs(np.sum(X_d.conj() * X_a, axis=0))
+    assert ov.min() > 1 - 1e-9
+    assert r_a.max() < 1e-10
+    # the paper's float64 residuals sit near 1e-15 (Tab. bench); the oracle's too
+    facts = _paper_facts()
+    assert r_a.max() < 100 * float(facts["fp64_resid_geosum_max"])
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+
+def _planted(monkeypatch, target, name, bad):
+    monkeypatch.setattr(target, name, bad)
+
+
+def test_planted_dropped_periodic_bond_is_caught(monkeypatch):
+    orig = model.diagonal_phases
+
+    def open_chain(L, J, h):
+        z = 1 - 2 * model.bit_table(L)
+        return J * (z[:, :-1] * z[:, 1:]).sum(1) + z.astype(float) @ np.asarray(h)
+
+    monkeypatch.setattr(model, "diagonal_phases", open_chain)
+    with pytest.raises(AssertionError):
+        test_apply_u_matches_dense_expm(5, 1.0, 0.9045)
+    monkeypatch.setattr(model, "diagonal_phases", orig)
+
+
+def test_planted_kick_sign_is_caught(monkeypatch):
+    orig = model.apply_kick
+    monkeypatch.setattr(model, "apply_kick", lambda psi, L, g: orig(psi, L, -g))
+    with pytest.raises(AssertionError):
+        test_apply_u_matches_dense_expm(4, 0.3, 0.2)
+
+
+def test_planted_kd_order_is_caught(monkeypatch):
+    # U = K D instead of D K: same spectrum, different operator
+    def apply_kd(self, psi):
+        return model.apply_kick(self.phase * psi, self.L, self.g)
+
+    monkeypatch.setattr(model.KickedIsing, "apply_u", apply_kd)
+    with pytest.raises(AssertionError):
+        test_apply_u_matches_dense_expm(3, 1.0, 0.9045)
+
+
+def test_planted_filter_off_by_one_is_caught(monkeypatch):
+    orig = geosum.filter_acc
+    monkeypatch.setattr(geosum, "filter_acc",
+                        lambda op, psi, phi, k: orig(op, psi, phi, k + 1))
+    with pytest.raises(AssertionError):
+        test_filter_closed_form_on_exact_eigenvectors()
+
+
+def test_planted_filter_phase_sign_is_caught(monkeypatch):
+    orig = geosum.zpow
+    monkeypatch.setattr(geosum, "zpow", lambda phi, j: orig(-phi, j))
+    with pytest.raises(AssertionError):
+        test_filter_peaks_at_target_eigenvalue()
+
+
+def test_planted_single_gram_schmidt_pass_is_caught(monkeypatch):
+    def cgs1(V, w):
+        h1 = V.T @ w                       # missing conjugate
+        w = w - V @ h1
+        beta = np.linalg.norm(w)
+        return h1, beta, w / beta
+
+    monkeypatch.setattr(krylov, "cgs2", cgs1)
+    with pytest.raises(AssertionError):
+        test_arnoldi_relation()
