@@ -1,0 +1,161 @@
+/*
+ * floquet.h -- C ABI of the GB300 geometric-sum polynomial-filter Floquet eigensolver.
+ *
+ * Method: D. J. Luitz, "Polynomial filter diagonalization of large Floquet unitary
+ * operators", arXiv:2102.05054. The eigenpairs of a Floquet unitary U closest to a target
+ * exp(i phi) on the unit circle are found by Arnoldi iteration (Sec. 4, Eq. arnoldi) on the
+ * geometric-sum filter g_k(U) (Sec. 3, Eq. geo), followed by Rayleigh quotients
+ * omega = <n|U|n> and residuals ||U|n> - omega|n>|| (Sec. 4, Eq. residual).
+ *
+ * Operator (a local Floquet operator with a cheap matrix-free product, as Sec. 2 requires):
+ *   U = D K,  K = exp(-i g sum_i X_i),  D = exp(-i sum_i (J Z_i Z_{i+1} + h_i Z_i)),
+ *   periodic chain of L qubits (bond (L-1, 0) included), 3 <= L <= 24.
+ *   Amplitude index s = sum_i b_i 2^i (qubit i = bit i), Z|0> = +|0>.
+ *
+ * Filter length: k is the NUMBER OF TERMS, g_k(U) = sum_{j=0}^{k-1} exp(-i j phi) U^j.
+ * (The paper's order-k filter, Eq. geo, has k+1 terms.)
+ *
+ * Layout: a state is d = 2^L complex numbers, interleaved (re, im); complex128 = two
+ * doubles, complex64 = two floats. A block of n states is column-major with leading
+ * dimension d (state j starts at element j*d).
+ *
+ * Pointers: "device" pointers are CUDA device (or managed) memory of the current device;
+ * "host" pointers are ordinary host memory. Arguments documented "host or device" are
+ * classified with cudaPointerGetAttributes. The caller owns every buffer it passes; the
+ * library owns the workspace it allocates inside a floquet_t (freed by floquet_destroy)
+ * and the scratch of a call (freed before the call returns).
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream). Calls that return
+ * host-visible results synchronise that stream before returning; the others are
+ * asynchronous with respect to the host.
+ *
+ * Errors: every call returns FLOQUET_OK (0) or a negative code; floquet_last_error()
+ * returns a thread-local message describing the last failure. No C++ exception crosses the
+ * ABI. After FLOQUET_ECUDA the CUDA context may be unusable.
+ */
+#ifndef FLOQUET_H
+#define FLOQUET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct floquet_op* floquet_t;
+
+enum floquet_status {
+  FLOQUET_OK = 0,
+  FLOQUET_EINVAL = -1,   /* invalid argument (size, pointer, enum) */
+  FLOQUET_ENOMEM = -2,   /* device or host allocation failed */
+  FLOQUET_ECUDA = -3,    /* a CUDA call or kernel failed */
+  FLOQUET_ENOCONV = -4,  /* eigensolver hit max_restarts; partial results returned */
+  FLOQUET_ETIMEOUT = -5  /* reserved: a bounded device-side wait gave up */
+};
+
+enum floquet_dtype { FLOQUET_C128 = 0, FLOQUET_C64 = 1 };
+
+/* Precision form of the eigensolver (arnoldi_eigs):
+ *   FLOQUET_FP64        -- filter sweeps U^j in complex128, FP64 Arnoldi;
+ *   FLOQUET_FILTER_FP32 -- filter sweeps in complex64 with complex64 accumulation, FP64
+ *                          Gram-Schmidt, Hessenberg/Schur, Ritz extraction and residuals,
+ *                          then an FP64 Rayleigh-Ritz polish of the returned eigenpairs
+ *                          (Sec. 4 footnote: one Ritz step with <n|U|m> on approximate
+ *                          eigenvectors) iterated with defect-corrected filtering until the
+ *                          U-residuals reach tol_resid. */
+enum floquet_precision { FLOQUET_FP64 = 0, FLOQUET_FILTER_FP32 = 1 };
+
+/* Filter formulation (filter_apply): both equal sum_{j<k} z^j U^j psi, z = exp(-i phi).
+ *   FLOQUET_FORM_ACC    -- psi_0 = psi, psi_{j+1} = U psi_j, acc += z^j psi_j: 4 d b bytes
+ *                          per U application (b = bytes per complex);
+ *   FLOQUET_FORM_HORNER -- acc <- psi + z U acc, k-1 times from acc = psi: 3 d b bytes
+ *                          per U application. */
+enum floquet_form { FLOQUET_FORM_ACC = 0, FLOQUET_FORM_HORNER = 1 };
+
+/* Create the operator U = D K (Sec. 2; model fixed above). h: host, L doubles, copied.
+ * Builds the diagonal-phase tables and the pass plan on the current device.
+ * EINVAL if L outside [3, 24] or h/out NULL; ENOMEM/ECUDA on allocation failure. */
+int floquet_create(int L, double J, double g, const double* h, floquet_t* out);
+
+/* Release the operator and all workspace it owns. NULL is accepted. */
+int floquet_destroy(floquet_t op);
+
+/* d = 2^L. */
+int floquet_dim(floquet_t op, int64_t* d);
+
+/* psi_out[:, j] = U psi_in[:, j] for j < nvec (the matrix-free product of Sec. 2 that
+ * Sec. 3 requires). psi_in, psi_out: device, nvec*d complex of `dtype`; may be equal
+ * (in place). Asynchronous on `stream`. */
+int floquet_apply_u(floquet_t op, const void* psi_in, void* psi_out, int nvec, int dtype,
+                    void* stream);
+
+/* psi_out[:, j] = g_k(U) psi_in[:, j] (Sec. 3, Eq. geo, k terms) for j < nvec.
+ * psi_in, psi_out: device, nvec*d complex of `dtype`, must not overlap. k >= 1.
+ * `form` selects the formulation (floquet_form). Asynchronous on `stream`; the k-step loop
+ * runs as a captured CUDA graph that is cached in `op` for the same (k, nvec, dtype, form). */
+int filter_apply(floquet_t op, double phi, int64_t k, const void* psi_in, void* psi_out,
+                 int nvec, int dtype, int form, void* stream);
+
+/* One classical Gram-Schmidt step with one full reorthogonalisation (CGS2) of Sec. 4's
+ * Arnoldi process: w <- (w - V V^H w) / beta, twice projected, for n >= 0 orthonormal
+ * columns V (device, d x n complex128, column-major, leading dimension d).
+ * w: device, d complex128, overwritten with the unit vector. h: host, n+1 complex128
+ * (2(n+1) doubles): the summed projection coefficients V^H w and, last, beta (real part).
+ * Synchronises `stream`. */
+int gram_schmidt(int64_t d, const void* V, int n, void* w, double* h, void* stream);
+
+/* Eigen-decomposition of a small general complex matrix on the device (the Hessenberg /
+ * Schur solve behind Sec. 4's Ritz pairs): A = Y diag(lambda) Y^{-1}.
+ * A: host or device, n x n complex128 column-major; lambda: host, n complex128; Y: host or
+ * device, n x n complex128 column-major, unit-norm columns. 1 <= n <= 512. Order of the
+ * eigenvalues: descending modulus. Synchronises `stream`. */
+int small_eig(int n, const void* A, double* lambda, void* Y, void* stream);
+
+/* Rayleigh quotients and residuals (Sec. 4, Eq. residual) of nvec vectors X (device, d x
+ * nvec complex128; normalised internally, X itself is not modified):
+ * omega_j = <x_j|U|x_j>/<x_j|x_j>, resid_j = ||U x_j - omega_j x_j|| / ||x_j||.
+ * omega: host, 2*nvec doubles; resid: host, nvec doubles. Synchronises `stream`. */
+int ritz_residuals(floquet_t op, const void* X, int nvec, double* omega, double* resid,
+                   void* stream);
+
+/* The eigensolver of Secs. 3-4: Krylov-Schur restarted Arnoldi on g_k(U) with CGS2,
+ * Krylov dimension m, keeping the nev eigenpairs of U whose eigenvalues are closest to
+ * exp(i phi) by wrapped angle |arg(omega e^{-i phi})| (ties: ascending arg), eigenvalues as
+ * Rayleigh quotients and residuals as in Eq. residual.
+ *   precision   -- floquet_precision;
+ *   tol         -- convergence tolerance of the Ritz values of g_k(U) relative to |theta|
+ *                  (<= 0: 1e-12 for FP64, 1e-7 for FILTER_FP32);
+ *   tol_resid   -- required U-residual of every returned pair (<= 0: 1e-10);
+ *   max_restarts-- restart limit (ENOCONV when reached, partial results returned);
+ *   v0          -- host or device, d complex128 start vector (need not be normalised).
+ * Outputs: evals host 2*nev doubles (re, im), sorted by closeness; evecs host or device
+ * d*nev complex128 (may be NULL); resid host nev doubles; n_conv host int: number of
+ * returned pairs meeting tol_resid. 1 <= nev < m <= min(d, 1024), 2 <= k.
+ * Synchronises `stream`. */
+int arnoldi_eigs(floquet_t op, double phi, int64_t k, int nev, int m, int precision,
+                 double tol, double tol_resid, int max_restarts, const void* v0,
+                 double* evals, void* evecs, double* resid, int* n_conv, void* stream);
+
+/* Many independent eigenproblems in lockstep on one GPU: R disorder realisations (h: host,
+ * R*L doubles, realisation r at h + r*L) times P targets (phis: host, P doubles), all with
+ * the same L, J, g, k, nev, m and the FP64 form. Problem q = r*P + p. v0: host or device,
+ * d complex128, shared start vector. Outputs (host): evals 2*nev*R*P doubles, resid
+ * nev*R*P, n_conv R*P; problem q's block starts at q*nev. Synchronises `stream`. */
+int arnoldi_eigs_batched(int L, double J, double g, const double* h, int R,
+                         const double* phis, int P, int64_t k, int nev, int m, double tol,
+                         double tol_resid, int max_restarts, const void* v0, double* evals,
+                         double* resid, int* n_conv, void* stream);
+
+/* Number of kernel launches issued by this library on the calling thread since the last
+ * call of floquet_reset_launch_count (graph replays count each kernel node). */
+int64_t floquet_launch_count(void);
+void floquet_reset_launch_count(void);
+
+/* Thread-local description of the last error ("" if none). Valid until the next call. */
+const char* floquet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLOQUET_H */

@@ -1,0 +1,229 @@
+// Internal declarations shared by the CUDA translation units of libfloquet.
+//
+// Model (Sec. 2 of Luitz, arXiv:2102.05054, with the kicked-Ising operator of this library):
+//   U = D K, K = prod_q exp(-i g X_q), D_s = exp(-i theta_s),
+//   theta_s = J sum_i z_i z_{i+1 mod L} + sum_i h_i z_i, z_i = 1 - 2 b_i(s).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/floquet.h"
+
+namespace fq {
+
+// ------------------------------------------------------------------ complex helpers
+
+template <typename Real> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename Real> using cplx = typename cplx_of<Real>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(double re, double im) {
+  C r;
+  r.x = re;
+  r.y = im;
+  return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+// conj(a) * b
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+  C r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.x * b.y - a.y * b.x;
+  return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) {
+  C r;
+  r.x = a.x + b.x;
+  r.y = a.y + b.y;
+  return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) {
+  C r;
+  r.x = a.x - b.x;
+  r.y = a.y - b.y;
+  return r;
+}
+// a + b * c
+template <typename C> __host__ __device__ __forceinline__ C cfma(C b, C c, C a) {
+  C r;
+  r.x = a.x + b.x * c.x - b.y * c.y;
+  r.y = a.y + b.x * c.y + b.y * c.x;
+  return r;
+}
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const char* fmt, ...);
+const char* get_error();
+extern thread_local int last_status;
+
+#define FQ_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t _e = (call);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      ::fq::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, \
+                      __LINE__);                                                       \
+      return FLOQUET_ECUDA;                                                            \
+    }                                                                                  \
+  } while (0)
+
+#define FQ_CHECK_LAUNCH()                                                             \
+  do {                                                                                \
+    cudaError_t _e = cudaGetLastError();                                              \
+    if (_e != cudaSuccess) {                                                          \
+      ::fq::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(_e),     \
+                      __FILE__, __LINE__);                                            \
+      return FLOQUET_ECUDA;                                                           \
+    }                                                                                 \
+  } while (0)
+
+#define FQ_TRY(expr)            \
+  do {                          \
+    int _s = (expr);            \
+    if (_s != FLOQUET_OK) return _s; \
+  } while (0)
+
+void count_launch(int64_t n = 1);
+
+// ------------------------------------------------------------------ U application passes
+
+// One pass over a state: the tile of 2^NB amplitudes is formed by global bits
+// [0, c) (coalesced "column" bits) and [start, start + NB - c); the CTA index supplies the
+// other bits, [c, start) then [start + NB - c, L). The pass applies the X kick of every
+// qubit in tile bits [kick_from, NB), i.e. qubits [0, NB) for the first pass
+// (kick_from = 0, c = NB) and qubits [start, start + NB - c) for a later pass (kick_from = c).
+struct Pass {
+  int NB, c, start, kick_from;
+};
+
+enum Epilogue {
+  EPI_STORE = 0,        // dst = K_pass src
+  EPI_PHASE = 1,        // dst = D K_pass src (last pass of U)
+  EPI_PHASE_ACC = 2,    // dst = D K_pass src; acc += coef[j] * dst
+  EPI_PHASE_HORNER = 3  // dst = psi_in + z * D K_pass src (src = dst = acc)
+};
+
+// Everything a pass kernel needs, passed by value.
+template <typename Real> struct PassArgs {
+  const cplx<Real>* src;
+  cplx<Real>* dst;
+  int64_t d;          // state length 2^L (stride between vectors)
+  int L, NB, c, start, kick_from, midbits, topshift;
+  Real tau;           // butterfly multiplier, |tau| <= 1
+  // diagonal phase: D_s * scale = tab_lo[s & (2^a - 1)] * tab_hi[((s >> (a-1)) << 1) | (s & 1)]
+  const cplx<Real>* tab_lo;
+  const cplx<Real>* tab_hi;
+  int a;
+  int64_t tab_lo_stride, tab_hi_stride;  // per problem
+  int vec_per_prob;
+  // accumulate / Horner epilogue
+  cplx<Real>* acc;
+  const cplx<Real>* coef;  // per vector: coef[vec * coef_stride + jstep]
+  int64_t coef_stride;
+  int jstep;
+  const cplx<Real>* psi_in;
+};
+
+// Launch one pass for `nvec` vectors. `swap` selects the cot form of the butterfly.
+template <typename Real>
+int launch_pass(const PassArgs<Real>& a, int epi, bool swap, int nvec, cudaStream_t st);
+
+// Elementwise helpers (uapply.cu)
+template <typename Rin, typename Rout>
+int launch_convert(const cplx<Rin>* in, cplx<Rout>* out, int64_t n, cudaStream_t st);
+// work = in (converted); acc = coef[vec*stride + 0] * in (converted), per vector of length d
+template <typename Rin, typename Rout>
+int launch_filter_init(const cplx<Rin>* in, int64_t in_stride, cplx<Rout>* work,
+                       cplx<Rout>* acc, const cplx<Rout>* coef, int64_t coef_stride, int64_t d,
+                       int nvec, cudaStream_t st);
+
+// ------------------------------------------------------------------ operator
+
+struct FilterGraph {
+  int64_t k;
+  int nvec, dtype, form;
+  const void* key_in;
+  void* key_out;
+  const void* key_coef;
+  cudaGraphExec_t exec;
+};
+
+struct BatchTables {
+  // phase tables for P problems (device), both precisions
+  double2* lo64 = nullptr;
+  double2* hi64 = nullptr;
+  float2* lo32 = nullptr;
+  float2* hi32 = nullptr;
+  int64_t lo_n = 0, hi_n = 0;
+  int a = 0;
+  int P = 0;
+};
+
+struct Plan {
+  std::vector<Pass> passes;  // first pass kicks [0, NB); the last applies the epilogue
+};
+
+}  // namespace fq
+
+struct floquet_op {
+  int L;
+  double J, g;
+  std::vector<double> h;  // L (or R*L for a batch)
+  int64_t d;
+  int nprob;              // problems sharing L, J, g (1 for floquet_create)
+  double tau;             // butterfly multiplier
+  bool swap;              // cot form
+  fq::BatchTables tabs;
+  fq::Plan plan64, plan32;
+  // filter workspace (lazily sized)
+  void* work = nullptr;
+  void* acc = nullptr;
+  void* psi_in_copy = nullptr;
+  size_t work_bytes = 0;
+  void* coef = nullptr;
+  size_t coef_bytes = 0;
+  double coef_phi = 0;
+  int64_t coef_k = -1;
+  int coef_dtype = -1, coef_nvec = -1, coef_form = -1;
+  std::vector<fq::FilterGraph> graphs;
+  cudaStream_t cap_stream = nullptr;  // capture/replay stream of the filter graphs
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+namespace fq {
+
+// Builds tables and plans for `nprob` problems (h: nprob * L doubles).
+int op_init(floquet_op* op, int L, double J, double g, const double* h, int nprob);
+void op_free(floquet_op* op);
+
+// U application on nvec vectors (vector v belongs to problem v / vec_per_prob).
+template <typename Real>
+int apply_u(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int nvec, int vec_per_prob,
+            cudaStream_t st);
+
+// Polynomial filter in the accumulate form, out_v = sum_{j<k} coef[v*k + j] U^j in_v, for
+// nvec vectors (in_v at in + v*in_stride, out_v at out + v*out_stride, type Rio); the
+// sweeps run in Real in the op's internal workspace. `use_graph` captures the k-step loop
+// once and replays it.
+template <typename Real, typename Rio>
+int filter_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio>* out,
+                int64_t out_stride, const cplx<Real>* coef, int64_t k, int nvec,
+                int vec_per_prob, bool use_graph, cudaStream_t st);
+
+// Horner form with one z per vector (zs: device, nvec complex of Real).
+template <typename Real, typename Rio>
+int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio>* out,
+                  int64_t out_stride, const cplx<Real>* zs, int64_t k, int nvec,
+                  int vec_per_prob, bool use_graph, cudaStream_t st);
+
+}  // namespace fq

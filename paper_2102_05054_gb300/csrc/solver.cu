@@ -1,0 +1,540 @@
+// Krylov-Schur restarted Arnoldi on the geometric-sum filter g_k(U) (Secs. 3-4 of Luitz,
+// arXiv:2102.05054), batched over independent problems that advance in lockstep.
+//
+// Per restart cycle and problem b:
+//   expansion   for j = p .. m-1: w = g_k(U_b) v_j (filter graph), CGS2 against V[:, :j+1]
+//               -> H[:j+2, j], v_{j+1};
+//   small solve H_m = Y diag(theta) Y^{-1} on the device (descending |theta|, the ARPACK
+//               'LM' order the paper uses), Ritz estimates |beta| |e_m^T y|;
+//   check       when the top nc >= nev+1 Ritz values are converged: Ritz vectors X = V Y,
+//               omega = <x|U|x>, r = ||U x - omega x|| (Eq. residual, FP64 U); the nev
+//               in-lobe eigenvalues closest to exp(i phi) are final once the nev-th has
+//               |g_k(omega)| above the smallest converged |theta| (every closer eigenvalue
+//               has a larger |g_k| and so is among the converged);
+//   restart     keep the p leading Ritz directions: Q = orth(Y[:, :p]), V <- V Q,
+//               H <- [Q^H H_m Q ; beta e_m^T Q] (a Krylov-Schur decomposition with a full
+//               p x p block; ARPACK's implicit restart keeps the same subspace).
+// The FILTER_FP32 form runs the filter sweeps in complex64 and everything else in FP64,
+// then polishes the returned pairs (polish()).
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "floquet_internal.cuh"
+#include "linalg.cuh"
+#include "solver.cuh"
+
+namespace fq {
+
+using cd = std::complex<double>;
+
+template <typename T> struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  int alloc(size_t count) {
+    if (count <= n) return FLOQUET_OK;
+    cudaFree(p);
+    p = nullptr;
+    n = 0;
+    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of %zu bytes failed", count * sizeof(T));
+      return FLOQUET_ENOMEM;
+    }
+    n = count;
+    return FLOQUET_OK;
+  }
+  ~DevBuf() { cudaFree(p); }
+};
+
+int DevVec::alloc(size_t count) {
+  if (count <= n) return FLOQUET_OK;
+  cudaFree(p);
+  p = nullptr;
+  n = 0;
+  if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes failed", count * sizeof(double2));
+    return FLOQUET_ENOMEM;
+  }
+  n = count;
+  return FLOQUET_OK;
+}
+DevVec::~DevVec() { cudaFree(p); }
+
+static double wrapped_angle(cd om, double phi) { return std::arg(om * std::polar(1.0, -phi)); }
+
+// |g_k(omega)| with omega rotated by exp(-i phi): (1 - w^k)/(1 - w) evaluated by the
+// recurrence g_{n+1} = g_n + w^n (no cancellation near w = 1)
+static cd gk_value(cd om, double phi, int64_t k) {
+  const cd w = om * std::polar(1.0, -phi);
+  const double a = std::abs(1.0 - w);
+  if (a > 1e-3) return (1.0 - std::pow(w, (double)k)) / (1.0 - w);
+  cd g = 0, wn = 1;
+  for (int64_t n = 0; n < k; ++n) {
+    g += wn;
+    wn *= w;
+  }
+  return g;
+}
+
+// Selection of the nev eigenvalues closest to exp(i phi): indices into om sorted by
+// (|arg|, arg), restricted to the main lobe |arg| < 2 pi / k.
+static std::vector<int> select_closest(const std::vector<cd>& om, double phi, int64_t k,
+                                       int nev, bool inlobe_only) {
+  std::vector<int> idx;
+  for (int i = 0; i < (int)om.size(); ++i) {
+    const double a = std::fabs(wrapped_angle(om[i], phi));
+    if (std::abs(om[i]) < 0.5) continue;  // not an eigenvalue of a unitary (degenerate vector)
+    if (!inlobe_only || a < 2 * M_PI / (double)k) idx.push_back(i);
+  }
+  std::sort(idx.begin(), idx.end(), [&](int x, int y) {
+    const double ax = wrapped_angle(om[x], phi), ay = wrapped_angle(om[y], phi);
+    if (std::fabs(ax) != std::fabs(ay)) return std::fabs(ax) < std::fabs(ay);
+    return ax < ay;
+  });
+  if ((int)idx.size() > nev) idx.resize(nev);
+  return idx;
+}
+
+__global__ void restart_h_kernel(const double2* __restrict__ Hold, int64_t ldh,
+                                 int64_t strideH, const double2* __restrict__ Bp,
+                                 int64_t strideB, const double2* __restrict__ Q, int64_t strideQ,
+                                 int m, int p, double2* __restrict__ Hnew) {
+  const int64_t b = blockIdx.x;
+  const double2 beta = Hold[b * strideH + (int64_t)(m - 1) * ldh + m];
+  double2* Hn = Hnew + b * strideH;
+  for (int64_t i = threadIdx.x; i < ldh * m; i += blockDim.x) {
+    const int r = (int)(i % ldh), c = (int)(i / ldh);
+    double2 v = make_double2(0, 0);
+    if (c < p && r < p) v = Bp[b * strideB + (int64_t)c * p + r];
+    if (c < p && r == p) v = cmul(beta, Q[b * strideQ + (int64_t)c * m + (m - 1)]);
+    Hn[i] = v;
+  }
+}
+
+__global__ void broadcast_kernel(const double2* __restrict__ v, double2* __restrict__ out,
+                                 int64_t d, int64_t stride) {
+  const int64_t b = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[b * stride + i] = v[i];
+}
+
+// ------------------------------------------------------------------ solver state
+
+struct KS {
+  floquet_op* op;
+  int B, vpp;  // problems; vectors of the op's tables per problem index (b / vpp = table)
+  int64_t d;
+  int m, nev;
+  int64_t k;
+  int precision;
+  double tol, tol_resid;
+  int max_restarts;
+  std::vector<double> phis;  // per problem
+  cudaStream_t st;
+  Workspace ws;
+  DevBuf<double2> V, V2, H, H2, w, lam, Y, Q, Bp, Tmp, eigw, X, W, R, Xs;
+  DevBuf<double> rq;
+  DevBuf<int> info;
+  DevBuf<double2> coef64;
+  DevBuf<float2> coef32;
+  int64_t strideV() const { return d * (m + 1); }
+  int64_t ldh() const { return m + 1; }
+  int64_t strideH() const { return (int64_t)(m + 1) * m; }
+};
+
+static int ks_alloc(KS& s) {
+  const size_t B = s.B, m = s.m, d = s.d;
+  FQ_TRY(s.V.alloc(B * d * (m + 1)));
+  FQ_TRY(s.V2.alloc(B * d * (m + 1)));
+  FQ_TRY(s.H.alloc(B * (m + 1) * m));
+  FQ_TRY(s.H2.alloc(B * (m + 1) * m));
+  FQ_TRY(s.w.alloc(B * d));
+  FQ_TRY(s.lam.alloc(B * m));
+  FQ_TRY(s.Y.alloc(B * m * m));
+  FQ_TRY(s.Q.alloc(B * m * m));
+  FQ_TRY(s.Bp.alloc(B * m * m));
+  FQ_TRY(s.Tmp.alloc(B * m * m));
+  FQ_TRY(s.eigw.alloc(B * small_eig_work_elems((int)m)));
+  FQ_TRY(s.info.alloc(B));
+  FQ_TRY(s.X.alloc(B * d * m));
+  FQ_TRY(s.W.alloc(B * d * m));
+  FQ_TRY(s.rq.alloc(B * m * 3));
+  // filter coefficients z_b^j = exp(-i j phi_b), float64 on the host
+  std::vector<double2> c64((size_t)B * s.k);
+  for (size_t b = 0; b < B; ++b)
+    for (int64_t j = 0; j < s.k; ++j) {
+      const double a = -s.phis[b] * (double)j;
+      c64[b * s.k + j] = make_double2(cos(a), sin(a));
+    }
+  if (s.precision == FLOQUET_FP64) {
+    FQ_TRY(s.coef64.alloc(c64.size()));
+    FQ_CUDA(cudaMemcpy(s.coef64.p, c64.data(), c64.size() * sizeof(double2),
+                       cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float2> c32(c64.size());
+    for (size_t i = 0; i < c64.size(); ++i)
+      c32[i] = make_float2((float)c64[i].x, (float)c64[i].y);
+    FQ_TRY(s.coef32.alloc(c32.size()));
+    FQ_CUDA(cudaMemcpy(s.coef32.p, c32.data(), c32.size() * sizeof(float2),
+                       cudaMemcpyHostToDevice));
+  }
+  return FLOQUET_OK;
+}
+
+// w_b = g_k(U_b) V_b[:, j]
+static int ks_filter(KS& s, int j) {
+  const double2* in = s.V.p + (int64_t)j * s.d;
+  if (s.precision == FLOQUET_FP64)
+    return filter_coef<double, double>(s.op, in, s.strideV(), s.w.p, s.d, s.coef64.p, s.k, s.B,
+                                       s.vpp, true, s.st);
+  return filter_coef<float, double>(s.op, in, s.strideV(), s.w.p, s.d, s.coef32.p, s.k, s.B,
+                                    s.vpp, true, s.st);
+}
+
+static int ks_expand(KS& s, int p) {
+  for (int j = p; j < s.m; ++j) {
+    FQ_TRY(ks_filter(s, j));
+    FQ_TRY(cgs2(s.ws, s.V.p, s.d, s.strideV(), j + 1, s.w.p, s.d, s.d, s.B,
+                s.H.p + (int64_t)j * s.ldh(), s.strideH(), s.V.p + (int64_t)(j + 1) * s.d,
+                s.strideV(), s.st));
+  }
+  return FLOQUET_OK;
+}
+
+// Ritz vectors X_b = V_b Y_b[:, :nx], then W = U X and (omega, resid) to host
+static int ks_ritz(KS& s, int nx, std::vector<double>& rq_host) {
+  FQ_TRY(gemm_nn(s.V.p, s.d, s.strideV(), s.Y.p, s.m, (int64_t)s.m * s.m, s.X.p, s.d,
+                 s.d * nx, s.d, s.m, nx, s.B, s.st));
+  FQ_TRY(apply_u<double>(s.op, s.X.p, s.W.p, s.B * nx, nx * s.vpp, s.st));
+  FQ_TRY(rayleigh_residual(s.ws, s.X.p, s.W.p, s.d, s.B * nx, s.rq.p, s.st));
+  rq_host.resize((size_t)3 * s.B * nx);
+  FQ_CUDA(cudaMemcpyAsync(rq_host.data(), s.rq.p, rq_host.size() * sizeof(double),
+                          cudaMemcpyDeviceToHost, s.st));
+  FQ_CUDA(cudaStreamSynchronize(s.st));
+  return FLOQUET_OK;
+}
+
+struct ProblemResult {
+  bool done = false;
+  std::vector<cd> omega;
+  std::vector<double> resid;
+  std::vector<int> cols;  // columns of X (within the problem's block) of the selected pairs
+  int nconv_ritz = 0;     // converged Ritz values of g_k used for the block
+};
+
+// Polish of the FILTER_FP32 result (one problem): defect-corrected filtering of the
+// Ritz block, alternating with FP64 Rayleigh-Ritz on [X, Y].
+int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double tol_resid,
+           int max_iter, double2* X, int nb, int64_t d, std::vector<cd>& omega_out,
+           std::vector<double>& resid_out, std::vector<int>& cols_out, int* iters,
+           cudaStream_t st);
+
+int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, int nev, int m,
+                 int precision, double tol, double tol_resid, int max_restarts,
+                 const double2* v0_dev, std::vector<KSOut>& out, cudaStream_t st,
+                 KSStats* stats) {
+  KS s;
+  s.op = op;
+  s.B = B;
+  s.vpp = vpp;
+  s.d = op->d;
+  s.m = m;
+  s.nev = nev;
+  s.k = k;
+  s.precision = precision;
+  s.tol = tol;
+  s.tol_resid = tol_resid;
+  s.max_restarts = max_restarts;
+  s.phis.assign(phis, phis + B);
+  s.st = st;
+  FQ_TRY(ks_alloc(s));
+  out.clear();
+  out.resize(B);
+
+  // v_0 = v0 / ||v0|| for every problem
+  {
+    const unsigned gx = (unsigned)std::min<int64_t>((s.d + 255) / 256, 1024);
+    broadcast_kernel<<<dim3(gx, B), 256, 0, st>>>(v0_dev, s.w.p, s.d, s.d);
+    count_launch();
+    FQ_CHECK_LAUNCH();
+    FQ_TRY(cgs2(s.ws, s.V.p, s.d, s.strideV(), 0, s.w.p, s.d, s.d, B, nullptr, 0, s.V.p,
+                s.strideV(), st));
+  }
+  FQ_CUDA(cudaMemsetAsync(s.H.p, 0, sizeof(double2) * (size_t)B * s.strideH(), st));
+
+  std::vector<ProblemResult> res(B);
+  std::vector<double2> lam_h((size_t)B * m), ylast((size_t)B * m), beta_h(B);
+  std::vector<double> rq_h;
+  int p = 0;
+  int restarts = 0;
+  bool all_done = false;
+  for (;; ++restarts) {
+    FQ_TRY(ks_expand(s, p));
+    if (stats) stats->expansions += (m - p);
+    FQ_TRY(small_eig_batched(s.H.p, s.ldh(), s.strideH(), m, B, s.lam.p, m, s.Y.p, m,
+                             (int64_t)m * m, s.eigw.p, s.info.p, st));
+    FQ_CUDA(cudaMemcpyAsync(lam_h.data(), s.lam.p, sizeof(double2) * B * m,
+                            cudaMemcpyDeviceToHost, st));
+    FQ_CUDA(cudaMemcpy2DAsync(ylast.data(), sizeof(double2), s.Y.p + (m - 1),
+                              sizeof(double2) * m, sizeof(double2), (size_t)B * m,
+                              cudaMemcpyDeviceToHost, st));
+    FQ_CUDA(cudaMemcpy2DAsync(beta_h.data(), sizeof(double2),
+                              s.H.p + (int64_t)(m - 1) * s.ldh() + m,
+                              sizeof(double2) * s.strideH(), sizeof(double2), B,
+                              cudaMemcpyDeviceToHost, st));
+    FQ_CUDA(cudaStreamSynchronize(st));
+    // converged prefix per problem
+    std::vector<int> nc(B, 0);
+    int nx = 0;
+    for (int b = 0; b < B; ++b) {
+      const double beta = std::abs(cd(beta_h[b].x, beta_h[b].y));
+      int c = 0;
+      while (c < m) {
+        const cd th(lam_h[(size_t)b * m + c].x, lam_h[(size_t)b * m + c].y);
+        const cd yl(ylast[(size_t)b * m + c].x, ylast[(size_t)b * m + c].y);
+        if (beta * std::abs(yl) > tol * std::abs(th)) break;
+        ++c;
+      }
+      nc[b] = c;
+      if (!res[b].done && c > nev) nx = std::max(nx, c);
+    }
+    if (nx > 0) {
+      FQ_TRY(ks_ritz(s, nx, rq_h));
+      for (int b = 0; b < B; ++b) {
+        if (res[b].done || nc[b] <= nev) continue;
+        std::vector<cd> om(nc[b]);
+        for (int i = 0; i < nc[b]; ++i) {
+          const double* q = &rq_h[3 * ((size_t)b * nx + i)];
+          om[i] = cd(q[0], q[1]);
+        }
+        const std::vector<int> sel = select_closest(om, s.phis[b], k, nev, true);
+        if ((int)sel.size() < nev) continue;
+        const double g_nev = std::abs(gk_value(om[sel.back()], s.phis[b], k));
+        const cd th_last(lam_h[(size_t)b * m + nc[b] - 1].x, lam_h[(size_t)b * m + nc[b] - 1].y);
+        if (!(g_nev > std::abs(th_last) * (1 + 1e-9))) continue;
+        bool resid_ok = true;
+        for (int i : sel) resid_ok &= rq_h[3 * ((size_t)b * nx + i) + 2] <= tol_resid;
+        if (precision == FLOQUET_FP64 && !resid_ok) continue;
+        ProblemResult& r = res[b];
+        r.done = true;
+        r.cols = sel;
+        r.nconv_ritz = nc[b];
+        r.omega.clear();
+        r.resid.clear();
+        for (int i : sel) {
+          r.omega.push_back(om[i]);
+          r.resid.push_back(rq_h[3 * ((size_t)b * nx + i) + 2]);
+        }
+        // keep the selected Ritz vectors (FP64 form) or the whole converged block (FP32
+        // form, for the polish) in the output slot of this problem
+        KSOut& o = out[b];
+        o.omega = r.omega;
+        o.resid = r.resid;
+        if (precision == FLOQUET_FP64) {
+          FQ_TRY(o.vecs.alloc((size_t)nev * s.d));
+          for (int i = 0; i < nev; ++i)
+            FQ_CUDA(cudaMemcpyAsync(o.vecs.p + (size_t)i * s.d,
+                                    s.X.p + ((size_t)b * nx + sel[i]) * s.d,
+                                    sizeof(double2) * s.d, cudaMemcpyDeviceToDevice, st));
+          o.cols.resize(nev);
+          std::iota(o.cols.begin(), o.cols.end(), 0);
+        } else {
+          o.nblock = nc[b];
+          FQ_TRY(o.vecs.alloc((size_t)nc[b] * s.d));
+          FQ_CUDA(cudaMemcpyAsync(o.vecs.p, s.X.p + (size_t)b * nx * s.d,
+                                  sizeof(double2) * s.d * nc[b], cudaMemcpyDeviceToDevice, st));
+          o.cols = sel;
+        }
+        o.converged = true;
+      }
+    }
+    all_done = true;
+    for (int b = 0; b < B; ++b) all_done &= res[b].done;
+    if (all_done || restarts >= max_restarts) break;
+
+    // ---- restart: keep p leading Ritz directions
+    int ncmax = 0;
+    for (int b = 0; b < B; ++b)
+      if (!res[b].done) ncmax = std::max(ncmax, nc[b]);
+    const int base = std::max(ncmax, nev);
+    p = base + (m - base) / 2;
+    p = std::min(p, m - std::max(2, m / 8));
+    p = std::max(p, 1);
+    FQ_TRY(small_orth_batched(s.Y.p, m, (int64_t)m * m, m, p, B, s.Q.p, m, (int64_t)m * m, st));
+    // V2[:, :p] = V[:, :m] Q ; V2[:, p] = V[:, m]
+    FQ_TRY(gemm_nn(s.V.p, s.d, s.strideV(), s.Q.p, m, (int64_t)m * m, s.V2.p, s.d, s.strideV(),
+                   s.d, m, p, B, st));
+    copy_matrix_launch(s.V.p + (int64_t)m * s.d, s.d, s.strideV(), s.V2.p + (int64_t)p * s.d,
+                       s.d, s.strideV(), (int)s.d, 1, B, st);
+    FQ_CHECK_LAUNCH();
+    std::swap(s.V.p, s.V2.p);
+    std::swap(s.V.n, s.V2.n);
+    // H2 = [Q^H H_m Q ; beta Q[m-1, :]]
+    FQ_TRY(small_gemm_batched('N', 'N', m, p, m, s.H.p, s.ldh(), s.strideH(), s.Q.p, m,
+                              (int64_t)m * m, s.Tmp.p, m, (int64_t)m * m, B, st));
+    FQ_TRY(small_gemm_batched('C', 'N', p, p, m, s.Q.p, m, (int64_t)m * m, s.Tmp.p, m,
+                              (int64_t)m * m, s.Bp.p, p, (int64_t)m * m, B, st));
+    restart_h_kernel<<<B, 256, 0, st>>>(s.H.p, s.ldh(), s.strideH(), s.Bp.p, (int64_t)m * m,
+                                        s.Q.p, (int64_t)m * m, m, p, s.H2.p);
+    count_launch();
+    FQ_CHECK_LAUNCH();
+    std::swap(s.H.p, s.H2.p);
+    std::swap(s.H.n, s.H2.n);
+    if (stats) stats->restarts = restarts + 1;
+  }
+  if (stats) stats->restarts = restarts;
+
+  // FP32 form: polish every converged problem in FP64
+  if (precision == FLOQUET_FILTER_FP32) {
+    for (int b = 0; b < B; ++b) {
+      KSOut& o = out[b];
+      if (!o.converged) continue;
+      std::vector<cd> om;
+      std::vector<double> rs;
+      std::vector<int> cols;
+      int it = 0;
+      FQ_TRY(polish(op, s.ws, s.phis[b], k, nev, tol_resid, 30, o.vecs.p, o.nblock, s.d, om, rs,
+                    cols, &it, st));
+      o.omega = om;
+      o.resid = rs;
+      o.cols = cols;
+      if (stats) stats->polish_iters = it;
+    }
+  }
+  return all_done ? FLOQUET_OK : FLOQUET_ENOCONV;
+}
+
+// ------------------------------------------------------------------ polish
+
+// a_l(omega) = z^{l+1} g_{k-1-l}(z omega), l = 0..k-2: the polynomial q with
+// g_k(U) - g_k(omega) = q(U) (U - omega), so that g_k(U) x = g_k(omega) x + q(U) r for
+// r = (U - omega) x. The FP32 sweeps then act on the small residual r only.
+static void defect_coefficients(cd omega, double phi, int64_t k, float2* out,
+                                cd* g_at_omega) {
+  const cd z = std::polar(1.0, -phi);
+  const cd w = z * omega;
+  // g_n(w) for n = 1 .. k by g_{n} = g_{n-1} + w^{n-1}
+  std::vector<cd> g(k + 1);
+  g[0] = 0;
+  cd wn = 1;
+  for (int64_t n = 1; n <= k; ++n) {
+    g[n] = g[n - 1] + wn;
+    wn *= w;
+  }
+  *g_at_omega = g[k];
+  for (int64_t l = 0; l + 1 < k; ++l) {
+    const cd a = std::polar(1.0, -phi * (double)(l + 1)) * g[k - 1 - l];
+    out[l] = make_float2((float)a.real(), (float)a.imag());
+  }
+}
+
+static int orthonormalize(Workspace& ws, double2* X, int n, int64_t d, cudaStream_t st) {
+  for (int j = 0; j < n; ++j)
+    FQ_TRY(cgs2(ws, X, d, 0, j, X + (int64_t)j * d, 0, d, 1, nullptr, 0, X + (int64_t)j * d, 0,
+                st));
+  return FLOQUET_OK;
+}
+
+int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double tol_resid,
+           int max_iter, double2* X0, int nb, int64_t d, std::vector<cd>& omega_out,
+           std::vector<double>& resid_out, std::vector<int>& cols_out, int* iters,
+           cudaStream_t st) {
+  const int n2 = 2 * nb;
+  DevBuf<double2> S, WS, Xn, G, Yg, lam, eigw, R, corr, gvals;
+  DevBuf<float2> coef;
+  DevBuf<double> rq;
+  DevBuf<int> info;
+  FQ_TRY(S.alloc((size_t)n2 * d));
+  FQ_TRY(WS.alloc((size_t)n2 * d));
+  FQ_TRY(Xn.alloc((size_t)n2 * d));
+  FQ_TRY(G.alloc((size_t)n2 * n2));
+  FQ_TRY(Yg.alloc((size_t)n2 * n2));
+  FQ_TRY(lam.alloc(n2));
+  FQ_TRY(eigw.alloc(small_eig_work_elems(n2)));
+  FQ_TRY(info.alloc(1));
+  FQ_TRY(R.alloc((size_t)nb * d));
+  FQ_TRY(corr.alloc((size_t)nb * d));
+  FQ_TRY(gvals.alloc(nb));
+  FQ_TRY(rq.alloc((size_t)3 * n2));
+  FQ_TRY(coef.alloc((size_t)nb * (k - 1)));
+  // S[:, :nb] = X0 (orthonormalised)
+  FQ_CUDA(cudaMemcpyAsync(S.p, X0, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
+  FQ_TRY(orthonormalize(ws, S.p, nb, d, st));
+  int ns = nb;  // columns of S in use
+  std::vector<double> rq_h(3 * n2);
+  std::vector<float2> coef_h((size_t)nb * (k - 1));
+  std::vector<double2> g_h(nb);
+  std::vector<double2> lam_h(n2);
+  for (int it = 0;; ++it) {
+    // Rayleigh-Ritz with U on span(S): G = S^H U S, G = Yg diag Yg^{-1}
+    FQ_TRY(apply_u<double>(op, S.p, WS.p, ns, ns, st));
+    FQ_TRY(gemm_cn(ws, S.p, d, 0, WS.p, d, 0, d, ns, ns, 1, G.p, ns, 0, st));
+    FQ_TRY(small_eig_batched(G.p, ns, 0, ns, 1, lam.p, 0, Yg.p, ns, 0, eigw.p, info.p, st));
+    FQ_CUDA(cudaMemcpyAsync(lam_h.data(), lam.p, sizeof(double2) * ns, cudaMemcpyDeviceToHost,
+                            st));
+    FQ_CUDA(cudaStreamSynchronize(st));
+    // keep the nb Ritz values with the largest |g_k(omega)| (the block the filter enhances)
+    std::vector<int> order(ns);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<double> gabs(ns);
+    for (int i = 0; i < ns; ++i) gabs[i] = std::abs(gk_value(cd(lam_h[i].x, lam_h[i].y), phi, k));
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gabs[a] > gabs[b]; });
+    order.resize(nb);
+    // Xn = S Yg[:, order], Wn = WS Yg[:, order]  (via a permuted copy of Yg into G)
+    for (int i = 0; i < nb; ++i)
+      FQ_CUDA(cudaMemcpyAsync(G.p + (size_t)i * ns, Yg.p + (size_t)order[i] * ns,
+                              sizeof(double2) * ns, cudaMemcpyDeviceToDevice, st));
+    FQ_TRY(gemm_nn(S.p, d, 0, G.p, ns, 0, Xn.p, d, 0, d, ns, nb, 1, st));
+    FQ_TRY(gemm_nn(WS.p, d, 0, G.p, ns, 0, corr.p, d, 0, d, ns, nb, 1, st));  // corr = U Xn
+    FQ_TRY(rayleigh_residual(ws, Xn.p, corr.p, d, nb, rq.p, st));
+    FQ_CUDA(cudaMemcpyAsync(rq_h.data(), rq.p, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost,
+                            st));
+    FQ_CUDA(cudaStreamSynchronize(st));
+    std::vector<cd> om(nb);
+    for (int i = 0; i < nb; ++i) om[i] = cd(rq_h[3 * i], rq_h[3 * i + 1]);
+    const std::vector<int> sel = select_closest(om, phi, k, nev, false);
+    double worst = 0;
+    for (int i : sel) worst = std::max(worst, rq_h[3 * i + 2]);
+    omega_out.clear();
+    resid_out.clear();
+    cols_out = sel;
+    for (int i : sel) {
+      omega_out.push_back(om[i]);
+      resid_out.push_back(rq_h[3 * i + 2]);
+    }
+    *iters = it;
+    if (worst <= tol_resid || it >= max_iter) {
+      FQ_CUDA(cudaMemcpyAsync(X0, Xn.p, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
+      break;
+    }
+    // R = U x - omega x; corr = q(U) R in complex64 sweeps; Y = g(omega) x + corr
+    FQ_TRY(residual_vectors(Xn.p, corr.p, R.p, d, nb, rq.p, st));
+    for (int i = 0; i < nb; ++i) {
+      cd gv;
+      defect_coefficients(om[i], phi, k, coef_h.data() + (size_t)i * (k - 1), &gv);
+      g_h[i] = make_double2(gv.real(), gv.imag());
+    }
+    FQ_CUDA(cudaMemcpyAsync(coef.p, coef_h.data(), sizeof(float2) * coef_h.size(),
+                            cudaMemcpyHostToDevice, st));
+    FQ_CUDA(cudaMemcpyAsync(gvals.p, g_h.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice,
+                            st));
+    FQ_TRY((filter_coef<float, double>(op, R.p, d, corr.p, d, coef.p, k - 1, nb, nb, true, st)));
+    FQ_TRY(axpy_cols(Xn.p, corr.p, d, nb, gvals.p, st));
+    // S = orth([Xn, Y])
+    FQ_CUDA(cudaMemcpyAsync(S.p, Xn.p, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
+    FQ_CUDA(cudaMemcpyAsync(S.p + (size_t)nb * d, corr.p, sizeof(double2) * nb * d,
+                            cudaMemcpyDeviceToDevice, st));
+    ns = n2;
+    FQ_TRY(orthonormalize(ws, S.p, ns, d, st));
+  }
+  return FLOQUET_OK;
+}
+
+}  // namespace fq

@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads, exports every
+function include/floquet.h declares, and rejects invalid arguments before touching the GPU."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "floquet.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2102_05054_gb300 import build, floquet
+    build.build()
+    return floquet.lib()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)
+    skip = {"if", "for", "while", "sizeof", "return", "defined"}
+    return sorted({n for n in names if n not in skip})
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ["floquet_create", "floquet_destroy", "floquet_apply_u", "filter_apply",
+              "gram_schmidt", "small_eig", "ritz_residuals", "arnoldi_eigs",
+              "arnoldi_eigs_batched", "floquet_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2102_05054_gb300 import floquet
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(floquet.SIGNATURES) >= set(_declared_functions())
+
+
+def test_create_rejects_bad_arguments(lib):
+    from paper_2102_05054_gb300 import floquet
+    h = np.zeros(30)
+    handle = ctypes.c_void_p()
+    for L in (2, 25, -1):
+        rc = lib.floquet_create(L, 1.0, 0.9, h.ctypes.data_as(floquet._dptr), ctypes.byref(handle))
+        assert rc == floquet.EINVAL
+        assert b"outside" in lib.floquet_last_error()
+    assert lib.floquet_create(4, 1.0, 0.9, None, ctypes.byref(handle)) == floquet.EINVAL
+    bad = np.array([0.0, np.nan, 0.0, 0.0])
+    assert lib.floquet_create(4, 1.0, 0.9, bad.ctypes.data_as(floquet._dptr),
+                              ctypes.byref(handle)) == floquet.EINVAL
+    assert lib.floquet_create(4, np.inf, 0.9, h.ctypes.data_as(floquet._dptr),
+                              ctypes.byref(handle)) == floquet.EINVAL
+
+
+def test_calls_reject_null_handles(lib):
+    from paper_2102_05054_gb300 import floquet
+    assert lib.floquet_destroy(None) == floquet.OK
+    assert lib.floquet_apply_u(None, None, None, 1, 0, None) == floquet.EINVAL
+    assert lib.filter_apply(None, 0.0, 4, None, None, 1, 0, 0, None) == floquet.EINVAL
+    ev = np.zeros(4)
+    nc = ctypes.c_int()
+    assert lib.arnoldi_eigs(None, 0.0, 8, 2, 4, 0, 0.0, 0.0, 1, None,
+                            ev.ctypes.data_as(floquet._dptr), None,
+                            ev.ctypes.data_as(floquet._dptr), ctypes.byref(nc),
+                            None) == floquet.EINVAL
+    assert lib.small_eig(0, None, None, None, None) == floquet.EINVAL
+    assert lib.small_eig(513, None, None, None, None) == floquet.EINVAL
+    assert lib.gram_schmidt(0, None, 0, None, None, None) == floquet.EINVAL
+
+
+def test_launch_counter_resets(lib):
+    lib.floquet_reset_launch_count()
+    assert lib.floquet_launch_count() == 0

@@ -1,0 +1,175 @@
+"""GPU parity of the Arnoldi pieces (rows A6-A9) against the CPU oracle, through the C ABI.
+
+Bars (from the spec contract): eigenvalues |d lambda| <= 1e-10, eigenvector overlaps
+|<v_ref|v>| >= 1 - 1e-9, residuals ||U v - omega v|| <= 1e-10. Gram-Schmidt and the small
+eigensolver are pure float64 and are held to ~1e-13 relative (a few hundred ulps of the
+problem's scale).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import krylov, model
+from paper_2102_05054_gb300 import inputs
+
+from gpu_util import from_dev, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _overlaps(A, B):
+    return np.abs(np.sum(A.conj() * B, axis=0)) / (np.linalg.norm(A, axis=0) *
+                                                 np.linalg.norm(B, axis=0))
+
+
+@pytest.mark.parametrize("d,n", [(1024, 0), (1024, 1), (4096, 17), (65536, 64), (3000, 5)])
+def test_gram_schmidt_matches_oracle(d, n):
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    rng = np.random.default_rng(d + n)
+    if n:
+        V, _ = np.linalg.qr(rng.standard_normal((d, n)) + 1j * rng.standard_normal((d, n)))
+    else:
+        V = np.zeros((d, 0), dtype=np.complex128)
+    w = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+    h_ref, beta_ref, q_ref = krylov.cgs2(V, w) if n else (np.zeros(0), np.linalg.norm(w),
+                                                           w / np.linalg.norm(w))
+    tV = to_dev(V if n else np.zeros((d, 1), dtype=np.complex128))
+    tw = to_dev(w)
+    h = floquet.gram_schmidt(tV, n, tw)
+    torch.cuda.synchronize()
+    assert np.abs(h[:n] - h_ref).max(initial=0) < 1e-13 * np.linalg.norm(w)
+    assert abs(h[n].real - beta_ref) < 1e-13 * np.linalg.norm(w)
+    assert np.abs(from_dev(tw) - q_ref).max() < 1e-13
+    if n:
+        assert np.abs(V.conj().T @ from_dev(tw)).max() < 1e-14
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 37, 64, 100, 160, 256])
+def test_small_eig_random(n):
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Af = np.asfortranarray(A)
+    Y = torch.empty((n, n), dtype=torch.complex128, device="cuda")  # column-major n x n
+    lam = floquet.small_eig(Af, Y)
+    Yh = Y.cpu().numpy().T
+    # A Y = Y diag(lam), unit columns, descending |lam|, same spectrum as LAPACK
+    assert np.abs(A @ Yh - Yh * lam).max() < 1e-12 * np.linalg.norm(A)
+    assert np.allclose(np.linalg.norm(Yh, axis=0), 1, atol=1e-13)
+    assert np.all(np.diff(np.abs(lam)) <= 1e-12)
+    ref = np.linalg.eigvals(A)
+    for x in lam:
+        assert np.min(np.abs(ref - x)) < 1e-10 * np.linalg.norm(A)
+
+
+def test_small_eig_structured():
+    # Hessenberg input (an Arnoldi projection) and a unitary with clustered spectrum
+    require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    L, k, m = 8, 16, 40
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 3))
+    from oracle import geosum
+    _, H = krylov.arnoldi(lambda x: geosum.filter_acc(op, x, 0.0, k),
+                          inputs.complex_gaussian(1 << L, 1), m)
+    Hm = np.asfortranarray(H[:m])
+    lam = floquet.small_eig(Hm)
+    ref = np.linalg.eigvals(Hm)
+    for x in lam:
+        assert np.min(np.abs(ref - x)) < 1e-11 * np.abs(ref).max()
+    U = model.KickedIsing(6, 1.0, 0.9045, inputs.disorder(6, 4.0, 5)).dense()
+    lam = floquet.small_eig(np.asfortranarray(U))
+    assert np.allclose(np.abs(lam), 1, atol=1e-12)
+    _ = floquet
+
+
+def test_ritz_residuals_matches_oracle():
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    L = 12
+    h = inputs.disorder(L, 1.0, 8)
+    fq = floquet.Floquet(L, 1.0, 0.9045, h)
+    op = model.KickedIsing(L, 1.0, 0.9045, h)
+    X = inputs.random_states(1 << L, 5, 3) * np.array([1, 2, 0.5, 3, 1])
+    om, res = fq.ritz_residuals(to_dev(X))
+    om_ref, res_ref, _ = krylov.rayleigh_residual(op, X)
+    assert np.abs(om - om_ref).max() < 1e-14
+    assert np.abs(res - res_ref).max() < 1e-13
+    _ = torch
+
+
+def _solve(L, J, g, W, seed, phi, k, nev, m, precision=0, **kw):
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    h = inputs.disorder(L, W, seed)
+    fq = floquet.Floquet(L, J, g, h)
+    op = model.KickedIsing(L, J, g, h)
+    v0 = to_dev(inputs.start_vector(L))
+    ev = torch.empty((nev, 1 << L), dtype=torch.complex128, device="cuda")
+    om, res, nconv, rc = fq.arnoldi_eigs(phi, k, nev, m, v0, precision=precision, evecs=ev, **kw)
+    return om, res, nconv, rc, from_dev(ev, 1 << L), op
+
+
+def _check_against_dense(om, res, X, op, phi, nev, tol_l=1e-10, tol_ov=1e-9, tol_r=1e-10):
+    om_d, X_d, _ = krylov.dense_eigs(op, phi, nev)
+    assert np.abs(om - om_d).max() < tol_l, np.abs(om - om_d).max()
+    assert _overlaps(X_d, X).min() > 1 - tol_ov
+    assert res.max() <= tol_r
+    # residuals recomputed by the oracle's own U
+    _, r_cpu, _ = krylov.rayleigh_residual(op, X)
+    assert r_cpu.max() <= tol_r
+
+
+def test_arnoldi_eigs_L10_config_fp64():
+    cfg = inputs.WORKLOADS["kicked_ising_L10"]
+    om, res, nconv, rc, X, op = _solve(cfg["L"], 1.0, 0.9045, cfg["W"], cfg["seed"], cfg["phi"],
+                                       cfg["k"], cfg["nev"], cfg["m"])
+    assert rc == 0 and nconv == cfg["nev"]
+    _check_against_dense(om, res, X, op, cfg["phi"], cfg["nev"])
+
+
+@pytest.mark.parametrize("phi", [0.0, 1.3, -2.9])
+def test_arnoldi_eigs_with_restarts(phi):
+    # a Krylov space too small for one build: the Krylov-Schur restarts must be exercised
+    om, res, nconv, rc, X, op = _solve(11, 1.0, 0.9045, 1.0, 4, phi, 128, 12, 30)
+    assert rc == 0 and nconv == 12
+    _check_against_dense(om, res, X, op, phi, 12)
+
+
+def test_arnoldi_eigs_fp32_filter_form_L12():
+    om, res, nconv, rc, X, op = _solve(12, 1.0, 0.9045, 1.0, 2, 0.0, 128, 24, 96, precision=1)
+    assert rc == 0 and nconv == 24
+    _check_against_dense(om, res, X, op, 0.0, 24)
+
+
+def test_arnoldi_eigs_special_case_g0_L16():
+    # g = 0: exact eigenvalues exp(-i theta_s) in closed form at L = 16 (the L16 workload size)
+    L, phi, k, nev, m = 16, math.pi / 3, 1024, 50, 160
+    om, res, nconv, rc, X, op = _solve(L, 1.0, 0.0, 2.0, 1, phi, k, nev, m)
+    lam = model.spectrum_g0(L, 1.0, inputs.disorder(L, 2.0, 1))
+    want = lam[krylov.select_closest(lam, phi, nev)]
+    assert rc == 0 and nconv == nev
+    assert np.abs(om - want).max() < 1e-10
+    assert res.max() < 1e-10
+
+
+def test_arnoldi_eigs_batched_matches_dense():
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    L, k, nev, m = 10, 64, 8, 48
+    hs, _ = inputs.batched_disorder(L, (0.5, 2.0), 2, 10)
+    phis = np.array([0.0, math.pi / 2, math.pi])
+    v0 = to_dev(inputs.start_vector(L))
+    om, res, nconv, rc = floquet.arnoldi_eigs_batched(L, 1.0, 0.9045, hs, phis, k, nev, m, v0)
+    assert rc == 0
+    for r in range(hs.shape[0]):
+        op = model.KickedIsing(L, 1.0, 0.9045, hs[r])
+        for p, phi in enumerate(phis):
+            om_d, _, _ = krylov.dense_eigs(op, phi, nev)
+            assert np.abs(om[r, p] - om_d).max() < 1e-10
+            assert res[r, p].max() < 1e-10
+            assert nconv[r, p] == nev
+    _ = torch

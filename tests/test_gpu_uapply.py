@@ -1,0 +1,188 @@
+"""GPU parity of the U application (rows A1-A3) and the geometric-sum filter (A4-A5)
+against the CPU oracle, through the C ABI.
+
+Tolerances (derived from the arithmetic): one U application rounds each amplitude about
+L + 3 times, so complex128 results agree with the float64 oracle to ~1e-15 relative and
+complex64 results to ~(L + 3) * 6e-8 relative. A k-term filter accumulates k such
+applications: relative error grows at most ~k times (complex128: < 1e-12 here; complex64:
+< 5e-7 * sqrt(k) * L in the norm, taken with margin).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import geosum, model
+from paper_2102_05054_gb300 import inputs
+
+from gpu_util import from_dev, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _make(L, J, g, W, seed):
+    from paper_2102_05054_gb300 import floquet
+    h = inputs.disorder(L, W, seed)
+    return floquet.Floquet(L, J, g, h), model.KickedIsing(L, J, g, h)
+
+
+@pytest.mark.parametrize("L", [3, 4, 5, 7, 10, 11, 12, 13, 14, 16])
+@pytest.mark.parametrize("g", [0.3, 0.9045])   # tan form (|tan g| < 1) and cot form
+def test_apply_u_c128_matches_oracle(L, g):
+    torch = require_gpu()
+    fq, op = _make(L, 1.0, g, 1.0, 100 + L)
+    X = inputs.random_states(1 << L, 3, 7)
+    t_in = to_dev(X, torch.complex128)
+    t_out = torch.empty_like(t_in)
+    fq.apply_u(t_in, t_out)
+    torch.cuda.synchronize()
+    got = from_dev(t_out, 1 << L)
+    want = op.apply_u_block(X)
+    assert np.abs(got - want).max() < 1e-13 * np.abs(want).max() * L
+
+
+@pytest.mark.parametrize("L", [3, 4, 6, 9, 12, 13, 15, 17])
+@pytest.mark.parametrize("g", [0.3, 0.9045, -2.2])
+def test_apply_u_c64_matches_oracle(L, g):
+    torch = require_gpu()
+    fq, op = _make(L, 0.8, g, 2.0, 200 + L)
+    X = inputs.random_states(1 << L, 2, 8)
+    t_in = to_dev(X, torch.complex64)
+    t_out = torch.empty_like(t_in)
+    fq.apply_u(t_in, t_out)
+    torch.cuda.synchronize()
+    got = from_dev(t_out, 1 << L)
+    want = op.apply_u_block(X)
+    assert _rel(got, want) < 2e-7 * (L + 3)
+
+
+@pytest.mark.parametrize("dtype_name", ["complex128", "complex64"])
+def test_apply_u_in_place_and_special_cases(dtype_name):
+    torch = require_gpu()
+    dt = getattr(torch, dtype_name)
+    tol = 1e-13 if dtype_name == "complex128" else 5e-6
+    for (L, J, g) in [(12, 1.0, 0.0), (13, 0.0, 0.7), (14, 1.0, math.pi / 2), (18, 1.0, 0.9045)]:
+        fq, op = _make(L, J, g, 1.0, 300 + L)
+        x = inputs.complex_gaussian(1 << L, 9)
+        t = to_dev(x, dt)
+        fq.apply_u(t, t)  # in place
+        torch.cuda.synchronize()
+        assert _rel(from_dev(t), op.apply_u(x)) < tol
+
+
+@pytest.mark.parametrize("L", [20])
+def test_apply_u_L20_both_dtypes(L):
+    # the bench configuration: L = 20, two passes per U (tile bits 12 + 8 for complex64,
+    # 11 + 9 for complex128)
+    torch = require_gpu()
+    fq, op = _make(L, 1.0, 0.9045, 1.0, 1)
+    x = inputs.complex_gaussian(1 << L, 5)
+    want = op.apply_u(x)
+    for dt, tol in [(torch.complex128, 1e-14), (torch.complex64, 5e-6)]:
+        t_in = to_dev(x, dt)
+        t_out = torch.empty_like(t_in)
+        fq.apply_u(t_in, t_out)
+        torch.cuda.synchronize()
+        assert _rel(from_dev(t_out), want) < tol
+    # unitarity at full size: ||U^5 psi|| = ||psi||
+    t = to_dev(x, torch.complex128)
+    for _ in range(5):
+        fq.apply_u(t, t)
+    torch.cuda.synchronize()
+    assert abs(torch.linalg.norm(t).item() - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("L,k,phi", [(6, 1, 0.0), (6, 2, 0.3), (10, 64, 0.0), (12, 37, 1.0),
+                                     (14, 50, math.pi / 3), (16, 20, 2.0)])
+@pytest.mark.parametrize("form", [0, 1])
+def test_filter_c128_matches_oracle(L, k, phi, form):
+    torch = require_gpu()
+    fq, op = _make(L, 1.0, 0.9045, 1.0, 400 + L)
+    X = inputs.random_states(1 << L, 2, 10)
+    t_in = to_dev(X, torch.complex128)
+    t_out = torch.empty_like(t_in)
+    fq.filter_apply(phi, k, t_in, t_out, form=form)
+    torch.cuda.synchronize()
+    got = from_dev(t_out, 1 << L)
+    want = np.stack([geosum.filter_acc(op, X[:, i], phi, k) for i in range(2)], axis=1)
+    assert _rel(got, want) < 1e-13 * k
+
+
+@pytest.mark.parametrize("L,k,phi", [(10, 64, 0.0), (13, 100, 0.5), (16, 40, math.pi / 3)])
+@pytest.mark.parametrize("form", [0, 1])
+def test_filter_c64_matches_oracle(L, k, phi, form):
+    torch = require_gpu()
+    fq, op = _make(L, 1.0, 0.9045, 1.0, 500 + L)
+    x = inputs.complex_gaussian(1 << L, 11)
+    t_in = to_dev(x, torch.complex64)
+    t_out = torch.empty_like(t_in)
+    fq.filter_apply(phi, k, t_in, t_out, form=form)
+    torch.cuda.synchronize()
+    want = geosum.filter_acc(op, x, phi, k)
+    assert _rel(from_dev(t_out), want) < 5e-7 * math.sqrt(k) * L
+
+
+def test_filter_repeat_uses_cached_graph_and_is_deterministic():
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    fq, _ = _make(12, 1.0, 0.9045, 1.0, 7)
+    x = to_dev(inputs.complex_gaussian(1 << 12, 3), torch.complex64)
+    a = torch.empty_like(x)
+    b = torch.empty_like(x)
+    fq.filter_apply(0.2, 33, x, a)
+    floquet.reset_launch_count()
+    fq.filter_apply(0.2, 33, x, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    # init + 32 steps of one pass + final conversion
+    assert floquet.launch_count() == 1 + 32 + 1
+
+
+@pytest.mark.parametrize("dtype_name,tol", [("complex128", 1e-13), ("complex64", 1e-6)])
+def test_filter_full_length_L20_on_exact_eigenvectors(dtype_name, tol):
+    # L = 20, k = 16384 (the large workload's filter) on exact eigenvectors from closed-form
+    # special cases: g = 0 (basis states) and J = 0 (product states). g_k(U) v = g_k(w) v with
+    # the closed form of Eq. geo2 (k-term reading).
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    dt = getattr(torch, dtype_name)
+    L, k, phi = 20, 16384, 0.0
+    d = 1 << L
+    # g = 0: basis state |s>
+    h = inputs.disorder(L, 1.0, 1)
+    fq = floquet.Floquet(L, 1.0, 0.0, h)
+    lam = model.spectrum_g0(L, 1.0, h)
+    s = int(np.argmin(np.abs(np.angle(lam))))  # closest to the target: largest |g_k|
+    e = np.zeros(d, dtype=np.complex128)
+    e[s] = 1.0
+    t_in = to_dev(e, dt)
+    t_out = torch.empty_like(t_in)
+    fq.filter_apply(phi, k, t_in, t_out)
+    torch.cuda.synchronize()
+    want = geosum.gk_closed(lam[s:s + 1], phi, k)[0] * e
+    # absolute error per unit-norm input: at most ~k times one application's rounding
+    assert np.linalg.norm(from_dev(t_out) - want) < tol * k
+    # J = 0: product of single-site eigenvectors
+    g = 0.9045
+    fq = floquet.Floquet(L, 0.0, g, h)
+    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    v = np.ones(1, dtype=np.complex128)
+    lam_v = 1.0 + 0j
+    for i in range(L):
+        u = np.diag([np.exp(-1j * h[i]), np.exp(1j * h[i])]) @ (np.cos(g) * np.eye(2)
+                                                                - 1j * np.sin(g) * X)
+        w, vecs = np.linalg.eig(u)
+        j = int(np.argmin(np.abs(np.angle(w))))
+        v = np.kron(vecs[:, j], v)  # qubit i on the higher bits of the kron
+        lam_v *= w[j]
+    t_in = to_dev(v, dt)
+    t_out = torch.empty_like(t_in)
+    fq.filter_apply(phi, k, t_in, t_out)
+    torch.cuda.synchronize()
+    want = geosum.gk_closed(np.array([lam_v]), phi, k)[0] * v
+    assert np.linalg.norm(from_dev(t_out) - want) < tol * k
