@@ -1,0 +1,328 @@
+"""Benchmark: time to the nev eigenpairs closest to exp(i phi) of the L = 20 kicked-Ising
+Floquet operator (residual <= 1e-10), with the filter's U-application throughput against
+the HBM roofline.
+
+One step = one complete solve of the workload through the C ABI: operator set-up, the
+Krylov-Schur Arnoldi on g_k(U) (filter sweeps, CGS2, small solve, restarts), Ritz vectors,
+Rayleigh quotients and residuals, and (FILTER_FP32 form) the FP64 polish. Inputs are
+synthetic: h_i ~ U[-1, 1] from a seeded generator, complex-Gaussian start vector.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+N > 1 runs independent replicas (one disorder realisation per rank; no data-path
+collective), launched with torch.distributed.run.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "L=20 time to nev eigenpairs (resid<=1e-10); U-apply GB/s vs HBM peak"
+UNIT = "s"
+WORKLOAD = "kicked_ising_L20"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cfg(args):
+    from paper_2102_05054_gb300 import inputs
+    c = dict(inputs.WORKLOADS[args.workload])
+    if args.precision:
+        c["precision"] = args.precision
+    return c
+
+
+def _total_u_applications(cfg, stats_apps):
+    return stats_apps
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2102_05054_gb300 import floquet, inputs
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = _cfg(args)
+    L, k, m, nev, phi = cfg["L"], cfg["k"], cfg["m"], cfg["nev"], cfg["phi"]
+    prec = floquet.FILTER_FP32 if cfg["precision"] == "filter_fp32" else floquet.FP64
+    d = 1 << L
+    h = inputs.disorder(L, cfg["W"], cfg["seed"] + rank)  # one realisation per replica
+    v0_host = inputs.start_vector(L)
+    v0 = torch.from_numpy(v0_host).to(dev)
+    evecs = torch.empty((nev, d), dtype=torch.complex128, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def one_solve():
+        with floquet.Floquet(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h) as fq:
+            om, res, nconv, rc = fq.arnoldi_eigs(phi, k, nev, m, v0, precision=prec,
+                                                 max_restarts=args.max_restarts, evecs=evecs)
+        return om, res, nconv, rc
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        one_solve()
+        flush.fill_(1.0)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    floquet.profile_enable(True)
+    floquet.reset_launch_count()
+    times = []
+    results = None
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        results = one_solve()
+        t1.record(stream)
+        barrier()
+        times.append(t0.elapsed_time(t1) / 1000.0)
+    launches = floquet.launch_count()
+    prof = floquet.profile_read()
+    floquet.profile_enable(False)
+    clocks = sampler.stop()
+
+    t_step = sum(times) / len(times)
+    if ws > 1:
+        t = torch.tensor([t_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    # e2e: the public C-ABI call with HOST buffers (h, v0 in; eigenvalues, residuals and
+    # eigenvectors out), host<->device copies inside the timed region
+    evecs_host = np.empty((nev, d), dtype=np.complex128)
+    barrier()
+    te = time.perf_counter()
+    with floquet.Floquet(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h) as fq:
+        om_e, res_e, nconv_e, rc_e = fq.arnoldi_eigs(phi, k, nev, m, v0_host, precision=prec,
+                                                     max_restarts=args.max_restarts,
+                                                     evecs=evecs_host)
+    barrier()
+    t_e2e = time.perf_counter() - te
+
+    om, res, nconv, rc = results
+    kind = "c64" if prec == floquet.FILTER_FP32 else "c128"
+    sweep_ms, u_apps, alg_bytes = prof[kind]
+    hbm, peak_kind = _peaks()
+    out = None
+    if rank == 0:
+        achieved = alg_bytes / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+        traffic = _ncu_traffic(L, kind)
+        out = {
+            "metric": METRIC, "value": round(t_step, 4), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 2),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 sweeps / f64 Arnoldi" if kind == "c64" else "c128/f64",
+            "data": "synthetic (seeded h_i ~ U[-1,1], complex-Gaussian start vector)",
+            "config": {"workload": args.workload, "L": L, "J": inputs.J_DEFAULT,
+                       "g": inputs.G_DEFAULT, "W": cfg["W"], "phi": phi, "k": k, "m": m,
+                       "nev": nev, "precision": cfg["precision"], "filter_form": "acc",
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "working set larger than L2 (Krylov basis 4 GiB) and a 256 MiB "
+                             "buffer written between steps"},
+            "result": {"status": rc, "n_conv": nconv, "max_resid": float(np.max(res)),
+                       "omega_first": [float(om[0].real), float(om[0].imag)]},
+            "e2e": {"value": round(t_e2e, 4), "unit": UNIT,
+                    "h2d_bytes_per_step": int(d * 16 + L * 8),
+                    "d2h_bytes_per_step": int(nev * d * 16 + nev * 24),
+                    "status": rc_e, "n_conv": nconv_e},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+                         "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4) if achieved else None,
+                         "traffic": traffic, "kernel": "U application (pass_kernel x2)",
+                         "per_launch_bytes": 4 * d * (8 if kind == "c64" else 16),
+                         "u_applications": int(u_apps), "sweep_s": round(sweep_ms / 1e3, 3),
+                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "gpu_launches": int(launches // max(1, args.steps)),
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(cfg, u_apps // max(1, args.steps), h,
+                                               seconds=args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def _ncu_traffic(L, kind):
+    """DRAM bytes per U application from the committed ncu summary, if one matches."""
+    p = os.path.join(ROOT, "profiles", f"pass_kernel_L{L}_{kind}_traffic.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f).get("dram_bytes_per_u_application")
+    return None
+
+
+def cpu_baseline(cfg, u_apps_per_solve, h, seconds=15.0):
+    """The oracle as it stands on the host cores: time oracle U applications at the
+    workload's L for ~`seconds`, then scale to the U applications one GPU solve performed
+    (the filter sweeps dominate the solve; CGS2 and the small solves are not counted, so the
+    CPU figure is a lower bound)."""
+    from oracle import model
+
+    from paper_2102_05054_gb300 import inputs
+    L = cfg["L"]
+    op = model.KickedIsing(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h)
+    psi = inputs.complex_gaussian(1 << L, 1)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds or n < 2:
+        psi = op.apply_u(psi)
+        n += 1
+    dt = (time.perf_counter() - t0) / n
+    total = dt * u_apps_per_solve
+    return {"value": round(total, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle U applications at L={L} ({dt:.3f} s each, numpy, one "
+                      f"thread) scaled to the {u_apps_per_solve} U applications of one GPU "
+                      f"solve; host has {os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on this machine's host cores, bounded sample per step."""
+    from oracle import model
+
+    from paper_2102_05054_gb300 import inputs
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    cfg = _cfg(args)
+    L, k, m = cfg["L"], cfg["k"], cfg["m"]
+    h = inputs.disorder(L, cfg["W"], cfg["seed"])
+    op = model.KickedIsing(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h)
+    # U applications of one solve: at least m filters of k - 1 applications (one Krylov build)
+    u_apps = m * (k - 1)
+    psi = inputs.complex_gaussian(1 << L, 1)
+    vals = []
+    for step in range(args.warmup + args.steps):
+        n = 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < args.ref_seconds or n < 1:
+            psi = op.apply_u(psi)
+            n += 1
+        if step >= args.warmup:
+            vals.append((time.perf_counter() - t0) / n * u_apps)
+    v = sum(vals) / len(vals)
+    out = {"metric": METRIC, "value": round(v, 1), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded h_i ~ U[-1,1])", "impl": "reference",
+           "config": {"workload": args.workload, "L": L, "k": k, "m": m, "nev": cfg["nev"],
+                      "parallelism": "host cores"},
+           "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"oracle U applications for ~{args.ref_seconds} s per "
+                                      f"step, scaled to m*(k-1) = {u_apps} applications "
+                                      f"(one Krylov build); host has {os.cpu_count()} cores"},
+           "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "filter_fp32"])
+    ap.add_argument("--max-restarts", type=int, default=30)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

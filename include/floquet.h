@@ -53,7 +53,13 @@ enum floquet_status {
   FLOQUET_ETIMEOUT = -5  /* reserved: a bounded device-side wait gave up */
 };
 
-enum floquet_dtype { FLOQUET_C128 = 0, FLOQUET_C64 = 1 };
+/* Element types of states passed across the ABI, and the precision of the U sweeps:
+ *   FLOQUET_C128    -- complex128 in and out, complex128 (FP64) sweeps;
+ *   FLOQUET_C64     -- complex64 in and out, complex64 (FP32) sweeps;
+ *   FLOQUET_C128_DF -- complex128 in and out, sweeps in double-float complex arithmetic
+ *                      (each real an unevaluated sum of two floats, ~48 significant bits,
+ *                      error-free transformations on the FP32 pipes). */
+enum floquet_dtype { FLOQUET_C128 = 0, FLOQUET_C64 = 1, FLOQUET_C128_DF = 2 };
 
 /* Precision form of the eigensolver (arnoldi_eigs):
  *   FLOQUET_FP64        -- filter sweeps U^j in complex128, FP64 Arnoldi;
@@ -63,7 +69,9 @@ enum floquet_dtype { FLOQUET_C128 = 0, FLOQUET_C64 = 1 };
  *                          (Sec. 4 footnote: one Ritz step with <n|U|m> on approximate
  *                          eigenvectors) iterated with defect-corrected filtering until the
  *                          U-residuals reach tol_resid. */
-enum floquet_precision { FLOQUET_FP64 = 0, FLOQUET_FILTER_FP32 = 1 };
+/*   FLOQUET_FILTER_DF   -- filter sweeps in double-float (FLOQUET_C128_DF), FP64 for the
+ *                          rest; no polish needed (sweep accuracy ~1e-14 per step). */
+enum floquet_precision { FLOQUET_FP64 = 0, FLOQUET_FILTER_FP32 = 1, FLOQUET_FILTER_DF = 2 };
 
 /* Filter formulation (filter_apply): both equal sum_{j<k} z^j U^j psi, z = exp(-i phi).
  *   FLOQUET_FORM_ACC    -- psi_0 = psi, psi_{j+1} = U psi_j, acc += z^j psi_j: 4 d b bytes
@@ -145,6 +153,17 @@ int arnoldi_eigs_batched(int L, double J, double g, const double* h, int R,
                          const double* phis, int P, int64_t k, int nev, int m, double tol,
                          double tol_resid, int max_restarts, const void* v0, double* evals,
                          double* resid, int* n_conv, void* stream);
+
+/* Measurement hook. While enabled (on != 0), every replay of a filter's k-step sweep graph is
+ * bracketed by CUDA events on the stream it runs on, and the library accumulates the
+ * elapsed device time, the number of U applications (vectors x steps) and their
+ * algorithmic bytes (4 d b per U application in the accumulate form, 3 d b in the Horner
+ * form; b = 16 for complex128, 8 for complex64), separately for complex64 (index 1) and
+ * complex128 (index 0) sweeps, double-float sweeps at index 2 (b = 16).
+ * floquet_profile_read synchronises the event pairs it reads and returns the totals since
+ * the last floquet_profile_enable(1); arrays of length 3. */
+int floquet_profile_enable(int on);
+int floquet_profile_read(double* sweep_ms, int64_t* u_applications, double* alg_bytes);
 
 /* Number of kernel launches issued by this library on the calling thread since the last
  * call of floquet_reset_launch_count (graph replays count each kernel node). */

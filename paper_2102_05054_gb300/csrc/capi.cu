@@ -13,6 +13,8 @@
 namespace fq {
 int64_t launch_count();
 void reset_launch_count();
+int profile_enable(int on);
+int profile_read(double* ms, int64_t* apps, double* bytes);
 }  // namespace fq
 
 using namespace fq;
@@ -34,12 +36,17 @@ static int clear_and(int rc) {
   return rc;
 }
 
+template <typename Real> static int dtype_code();
+template <> int dtype_code<float>() { return FLOQUET_C64; }
+template <> int dtype_code<double>() { return FLOQUET_C128; }
+template <> int dtype_code<dfloat>() { return FLOQUET_C128_DF; }
+
 // Coefficients z^j = exp(-i j phi) in float64 (no recurrence), then rounded to Real.
 template <typename Real>
 static int upload_geometric_coef(floquet_op* op, double phi, int64_t k, int nvec,
                                  cudaStream_t st) {
   const size_t bytes = (size_t)k * nvec * sizeof(cplx<Real>);
-  const int dt = sizeof(Real) == 4 ? FLOQUET_C64 : FLOQUET_C128;
+  const int dt = dtype_code<Real>();
   if (op->coef && op->coef_bytes >= bytes && op->coef_phi == phi && op->coef_k == k &&
       op->coef_dtype == dt && op->coef_nvec == nvec && op->coef_form == FLOQUET_FORM_ACC)
     return FLOQUET_OK;
@@ -54,7 +61,7 @@ static int upload_geometric_coef(floquet_op* op, double phi, int64_t k, int nvec
   std::vector<cplx<Real>> h((size_t)k * nvec);
   for (int64_t j = 0; j < k; ++j) {
     const double ang = -phi * (double)j;
-    const cplx<Real> z = mk<cplx<Real>>(cos(ang), sin(ang));
+    const cplx<Real> z = from_d2<Real>(make_double2(cos(ang), sin(ang)));
     for (int v = 0; v < nvec; ++v) h[(size_t)v * k + j] = z;
   }
   FQ_CUDA(cudaStreamSynchronize(st));
@@ -70,7 +77,7 @@ static int upload_geometric_coef(floquet_op* op, double phi, int64_t k, int nvec
 template <typename Real>
 static int upload_horner_z(floquet_op* op, double phi, int nvec, cudaStream_t st) {
   const size_t bytes = (size_t)nvec * sizeof(cplx<Real>);
-  const int dt = sizeof(Real) == 4 ? FLOQUET_C64 : FLOQUET_C128;
+  const int dt = dtype_code<Real>();
   if (op->coef && op->coef_bytes >= bytes && op->coef_phi == phi && op->coef_dtype == dt &&
       op->coef_nvec == nvec && op->coef_form == FLOQUET_FORM_HORNER)
     return FLOQUET_OK;
@@ -82,7 +89,7 @@ static int upload_horner_z(floquet_op* op, double phi, int nvec, cudaStream_t st
     FQ_CUDA(cudaMalloc(&op->coef, bytes));
     op->coef_bytes = bytes;
   }
-  std::vector<cplx<Real>> h(nvec, mk<cplx<Real>>(cos(-phi), sin(-phi)));
+  std::vector<cplx<Real>> h(nvec, from_d2<Real>(make_double2(cos(-phi), sin(-phi))));
   FQ_CUDA(cudaStreamSynchronize(st));
   FQ_CUDA(cudaMemcpy(op->coef, h.data(), bytes, cudaMemcpyHostToDevice));
   op->coef_phi = phi;
@@ -93,19 +100,23 @@ static int upload_horner_z(floquet_op* op, double phi, int nvec, cudaStream_t st
   return FLOQUET_OK;
 }
 
-template <typename Real>
+template <typename Real, typename Rio>
 static int filter_apply_t(floquet_t op, double phi, int64_t k, const void* in, void* out,
                           int nvec, int form, cudaStream_t st) {
   using C = cplx<Real>;
+  using CIO = cplx<Rio>;
   if (form == FLOQUET_FORM_ACC) {
     FQ_TRY(upload_geometric_coef<Real>(op, phi, k, nvec, st));
-    return filter_coef<Real, Real>(op, (const C*)in, op->d, (C*)out, op->d, (const C*)op->coef,
-                                   k, nvec, nvec, true, st);
+    return filter_coef<Real, Rio>(op, (const CIO*)in, op->d, (CIO*)out, op->d,
+                                  (const C*)op->coef, k, nvec, nvec, true, st);
   }
   FQ_TRY(upload_horner_z<Real>(op, phi, nvec, st));
-  return filter_horner<Real, Real>(op, (const C*)in, op->d, (C*)out, op->d,
-                                   (const C*)op->coef, k, nvec, nvec, true, st);
+  return filter_horner<Real, Rio>(op, (const CIO*)in, op->d, (CIO*)out, op->d,
+                                  (const C*)op->coef, k, nvec, nvec, true, st);
 }
+
+// U applied with double-float sweeps to complex128 states (through a float4 copy)
+static int apply_u_df(floquet_t op, const double2* in, double2* out, int nvec, cudaStream_t st);
 
 
 // True if p is device (or managed) memory of some device; false for host memory.
@@ -179,6 +190,18 @@ static int solve_and_copy(floquet_op* op, int B, int vpp, const double* phis, in
   return rc;
 }
 
+static int apply_u_df(floquet_t op, const double2* in, double2* out, int nvec, cudaStream_t st) {
+  const int64_t n = (int64_t)nvec * op->d;
+  Tmp buf;
+  FQ_TRY(buf.alloc(sizeof(float4) * n));
+  float4* b = (float4*)buf.p;
+  FQ_TRY((launch_convert<double, dfloat>(in, b, n, st)));
+  FQ_TRY(apply_u<dfloat>(op, b, b, nvec, nvec, st));
+  FQ_TRY((launch_convert<dfloat, double>(b, out, n, st)));
+  FQ_CUDA(cudaStreamSynchronize(st));  // the scratch is freed on return
+  return FLOQUET_OK;
+}
+
 extern "C" {
 
 int floquet_create(int L, double J, double g, const double* h, floquet_t* out) {
@@ -242,6 +265,8 @@ int floquet_apply_u(floquet_t op, const void* psi_in, void* psi_out, int nvec, i
     rc = apply_u<double>(op, (const double2*)psi_in, (double2*)psi_out, nvec, nvec, st);
   else if (dtype == FLOQUET_C64)
     rc = apply_u<float>(op, (const float2*)psi_in, (float2*)psi_out, nvec, nvec, st);
+  else if (dtype == FLOQUET_C128_DF)
+    rc = apply_u_df(op, (const double2*)psi_in, (double2*)psi_out, nvec, st);
   else {
     set_error("floquet_apply_u: bad dtype %d", dtype);
     return FLOQUET_EINVAL;
@@ -265,7 +290,7 @@ int filter_apply(floquet_t op, double phi, int64_t k, const void* psi_in, void* 
     set_error("filter_apply: bad form %d", form);
     return FLOQUET_EINVAL;
   }
-  const size_t esz = dtype == FLOQUET_C128 ? 16 : 8;
+  const size_t esz = dtype == FLOQUET_C64 ? 8 : 16;
   const char* a = (const char*)psi_in;
   const char* b = (const char*)psi_out;
   const size_t bytes = (size_t)nvec * op->d * esz;
@@ -276,9 +301,11 @@ int filter_apply(floquet_t op, double phi, int64_t k, const void* psi_in, void* 
   cudaStream_t st = (cudaStream_t)stream;
   int rc;
   if (dtype == FLOQUET_C128)
-    rc = filter_apply_t<double>(op, phi, k, psi_in, psi_out, nvec, form, st);
+    rc = filter_apply_t<double, double>(op, phi, k, psi_in, psi_out, nvec, form, st);
   else if (dtype == FLOQUET_C64)
-    rc = filter_apply_t<float>(op, phi, k, psi_in, psi_out, nvec, form, st);
+    rc = filter_apply_t<float, float>(op, phi, k, psi_in, psi_out, nvec, form, st);
+  else if (dtype == FLOQUET_C128_DF)
+    rc = filter_apply_t<dfloat, double>(op, phi, k, psi_in, psi_out, nvec, form, st);
   else {
     set_error("filter_apply: bad dtype %d", dtype);
     return FLOQUET_EINVAL;
@@ -364,7 +391,9 @@ int ritz_residuals(floquet_t op, const void* X, int nvec, double* omega, double*
 
 static int check_eig_args(int64_t d, int64_t k, int nev, int m, int precision, int max_restarts) {
   if (k < 2 || nev < 1 || m <= nev || m > 512 || (int64_t)m > d || max_restarts < 0 ||
-      (precision != FLOQUET_FP64 && precision != FLOQUET_FILTER_FP32) || k > (1LL << 24)) {
+      (precision != FLOQUET_FP64 && precision != FLOQUET_FILTER_FP32 &&
+       precision != FLOQUET_FILTER_DF) ||
+      k > (1LL << 24)) {
     set_error("eigensolver: need 2 <= k <= 2^24, 1 <= nev < m <= min(d, 512), max_restarts >= "
               "0, valid precision (k=%lld nev=%d m=%d precision=%d)",
               (long long)k, nev, m, precision);
@@ -382,7 +411,7 @@ int arnoldi_eigs(floquet_t op, double phi, int64_t k, int nev, int m, int precis
     return FLOQUET_EINVAL;
   }
   FQ_TRY(check_eig_args(op->d, k, nev, m, precision, max_restarts));
-  if (tol <= 0) tol = precision == FLOQUET_FP64 ? 1e-12 : 1e-6;
+  if (tol <= 0) tol = precision == FLOQUET_FILTER_FP32 ? 1e-6 : 1e-12;
   if (tol_resid <= 0) tol_resid = 1e-10;
   const int rc = solve_and_copy(op, 1, 1, &phi, k, nev, m, precision, tol, tol_resid,
                                 max_restarts, v0, evals, evecs, resid, n_conv,
@@ -418,6 +447,11 @@ int arnoldi_eigs_batched(int L, double J, double g, const double* h, int R, cons
   if (rc == FLOQUET_ENOCONV) set_error("arnoldi_eigs_batched: max_restarts reached");
   return rc == FLOQUET_OK ? clear_and(rc) : rc;
   FQ_GUARD_END
+}
+
+int floquet_profile_enable(int on) { return profile_enable(on); }
+int floquet_profile_read(double* sweep_ms, int64_t* u_applications, double* alg_bytes) {
+  return profile_read(sweep_ms, u_applications, alg_bytes);
 }
 
 int64_t floquet_launch_count(void) { return launch_count(); }

@@ -17,10 +17,45 @@ namespace fq {
 
 // ------------------------------------------------------------------ complex helpers
 
+// Sweep precisions: float (complex64), double (complex128) and dfloat, a tag for
+// double-float arithmetic: each real number is an unevaluated sum hi + lo of two floats
+// (|lo| <= ulp(hi)/2), about 48 significant bits, computed on the FP32 pipes with
+// error-free transformations. A complex dfloat is a float4 (re.hi, re.lo, im.hi, im.lo).
+struct dfloat {};
+
 template <typename Real> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
 template <> struct cplx_of<double> { using type = double2; };
+template <> struct cplx_of<dfloat> { using type = float4; };
 template <typename Real> using cplx = typename cplx_of<Real>::type;
+
+// Real scalars of each sweep precision (the butterfly multiplier tau).
+template <typename Real> struct scal_of { using type = Real; };
+template <> struct scal_of<dfloat> { using type = float2; };
+template <typename Real> using scal = typename scal_of<Real>::type;
+
+// complex value <-> (double re, double im)
+__host__ __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__host__ __device__ __forceinline__ double2 to_d2(float4 a) {
+  return make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+}
+template <typename Real> __host__ __device__ __forceinline__ cplx<Real> from_d2(double2 a);
+template <> __host__ __device__ __forceinline__ float2 from_d2<float>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+template <> __host__ __device__ __forceinline__ double2 from_d2<double>(double2 a) { return a; }
+template <> __host__ __device__ __forceinline__ float4 from_d2<dfloat>(double2 a) {
+  const float rh = (float)a.x, ih = (float)a.y;
+  return make_float4(rh, (float)(a.x - (double)rh), ih, (float)(a.y - (double)ih));
+}
+template <typename Real> __host__ __device__ __forceinline__ scal<Real> scal_from(double t);
+template <> __host__ __device__ __forceinline__ float scal_from<float>(double t) { return (float)t; }
+template <> __host__ __device__ __forceinline__ double scal_from<double>(double t) { return t; }
+template <> __host__ __device__ __forceinline__ float2 scal_from<dfloat>(double t) {
+  const float h = (float)t;
+  return make_float2(h, (float)(t - (double)h));
+}
 
 template <typename C> __host__ __device__ __forceinline__ C mk(double re, double im) {
   C r;
@@ -119,7 +154,7 @@ template <typename Real> struct PassArgs {
   cplx<Real>* dst;
   int64_t d;          // state length 2^L (stride between vectors)
   int L, NB, c, start, kick_from, midbits, topshift;
-  Real tau;           // butterfly multiplier, |tau| <= 1
+  scal<Real> tau;     // butterfly multiplier, |tau| <= 1
   // diagonal phase: D_s * scale = tab_lo[s & (2^a - 1)] * tab_hi[((s >> (a-1)) << 1) | (s & 1)]
   const cplx<Real>* tab_lo;
   const cplx<Real>* tab_hi;
@@ -164,6 +199,8 @@ struct BatchTables {
   double2* hi64 = nullptr;
   float2* lo32 = nullptr;
   float2* hi32 = nullptr;
+  float4* lodf = nullptr;
+  float4* hidf = nullptr;
   int64_t lo_n = 0, hi_n = 0;
   int a = 0;
   int P = 0;

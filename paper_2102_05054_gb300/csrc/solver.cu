@@ -144,6 +144,7 @@ struct KS {
   DevBuf<int> info;
   DevBuf<double2> coef64;
   DevBuf<float2> coef32;
+  DevBuf<float4> coefdf;
   int64_t strideV() const { return d * (m + 1); }
   int64_t ldh() const { return m + 1; }
   int64_t strideH() const { return (int64_t)(m + 1) * m; }
@@ -177,6 +178,12 @@ static int ks_alloc(KS& s) {
     FQ_TRY(s.coef64.alloc(c64.size()));
     FQ_CUDA(cudaMemcpy(s.coef64.p, c64.data(), c64.size() * sizeof(double2),
                        cudaMemcpyHostToDevice));
+  } else if (s.precision == FLOQUET_FILTER_DF) {
+    std::vector<float4> cdf(c64.size());
+    for (size_t i = 0; i < c64.size(); ++i) cdf[i] = from_d2<dfloat>(c64[i]);
+    FQ_TRY(s.coefdf.alloc(cdf.size()));
+    FQ_CUDA(cudaMemcpy(s.coefdf.p, cdf.data(), cdf.size() * sizeof(float4),
+                       cudaMemcpyHostToDevice));
   } else {
     std::vector<float2> c32(c64.size());
     for (size_t i = 0; i < c64.size(); ++i)
@@ -193,6 +200,9 @@ static int ks_filter(KS& s, int j) {
   const double2* in = s.V.p + (int64_t)j * s.d;
   if (s.precision == FLOQUET_FP64)
     return filter_coef<double, double>(s.op, in, s.strideV(), s.w.p, s.d, s.coef64.p, s.k, s.B,
+                                       s.vpp, true, s.st);
+  if (s.precision == FLOQUET_FILTER_DF)
+    return filter_coef<dfloat, double>(s.op, in, s.strideV(), s.w.p, s.d, s.coefdf.p, s.k, s.B,
                                        s.vpp, true, s.st);
   return filter_coef<float, double>(s.op, in, s.strideV(), s.w.p, s.d, s.coef32.p, s.k, s.B,
                                     s.vpp, true, s.st);
@@ -321,7 +331,7 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
         if (!(g_nev > std::abs(th_last) * (1 + 1e-9))) continue;
         bool resid_ok = true;
         for (int i : sel) resid_ok &= rq_h[3 * ((size_t)b * nx + i) + 2] <= tol_resid;
-        if (precision == FLOQUET_FP64 && !resid_ok) continue;
+        if (precision != FLOQUET_FILTER_FP32 && !resid_ok) continue;
         ProblemResult& r = res[b];
         r.done = true;
         r.cols = sel;
@@ -337,7 +347,7 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
         KSOut& o = out[b];
         o.omega = r.omega;
         o.resid = r.resid;
-        if (precision == FLOQUET_FP64) {
+        if (precision != FLOQUET_FILTER_FP32) {
           FQ_TRY(o.vecs.alloc((size_t)nev * s.d));
           for (int i = 0; i < nev; ++i)
             FQ_CUDA(cudaMemcpyAsync(o.vecs.p + (size_t)i * s.d,

@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "floquet_internal.cuh"
 
@@ -48,6 +49,77 @@ void set_error(const char* fmt, ...) {
 }
 const char* get_error() { return g_err; }
 
+// ------------------------------------------------------------------ sweep profiling
+
+struct SweepEvent {
+  cudaEvent_t a, b;
+  int kind;  // 0 complex128, 1 complex64
+  int64_t u_apps;
+  double bytes;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<SweepEvent> g_prof_pending;
+static double g_prof_ms[3] = {0, 0, 0};
+static int64_t g_prof_apps[3] = {0, 0, 0};
+static double g_prof_bytes[3] = {0, 0, 0};
+
+int profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& e : g_prof_pending) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  g_prof_pending.clear();
+  g_prof_on = on != 0;
+  for (int i = 0; i < 3; ++i) {
+    g_prof_ms[i] = 0;
+    g_prof_apps[i] = 0;
+    g_prof_bytes[i] = 0;
+  }
+  return FLOQUET_OK;
+}
+
+int profile_read(double* ms, int64_t* apps, double* bytes) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& e : g_prof_pending) {
+    FQ_CUDA(cudaEventSynchronize(e.b));
+    float t = 0;
+    FQ_CUDA(cudaEventElapsedTime(&t, e.a, e.b));
+    g_prof_ms[e.kind] += t;
+    g_prof_apps[e.kind] += e.u_apps;
+    g_prof_bytes[e.kind] += e.bytes;
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  g_prof_pending.clear();
+  for (int i = 0; i < 3; ++i) {
+    if (ms) ms[i] = g_prof_ms[i];
+    if (apps) apps[i] = g_prof_apps[i];
+    if (bytes) bytes[i] = g_prof_bytes[i];
+  }
+  return FLOQUET_OK;
+}
+
+static bool profile_begin(cudaStream_t s, cudaEvent_t* a) {
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return false;
+  }
+  if (cudaEventCreate(a) != cudaSuccess) return false;
+  cudaEventRecord(*a, s);
+  return true;
+}
+
+static void profile_end(cudaStream_t s, cudaEvent_t a, int kind, int64_t u_apps,
+                        double bytes) {
+  cudaEvent_t b;
+  if (cudaEventCreate(&b) != cudaSuccess) return;
+  cudaEventRecord(b, s);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_pending.push_back(SweepEvent{a, b, kind, u_apps, bytes});
+}
+
 void count_launch(int64_t n) {
   std::lock_guard<std::mutex> lk(g_launch_mu);
   g_launches += n;
@@ -59,6 +131,81 @@ int64_t launch_count() {
 void reset_launch_count() {
   std::lock_guard<std::mutex> lk(g_launch_mu);
   g_launches = 0;
+}
+
+// ------------------------------------------------------------------ double-float arithmetic
+
+// Error-free transformations on the FP32 pipes (Dekker / Knuth two-sum and an FMA-based
+// two-product). The _rn intrinsics keep the compiler from contracting or reassociating.
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+// x + t * y for double-float x, t, y
+__device__ __forceinline__ float2 df_fma(float2 t, float2 y, float2 x) {
+  const float p = __fmul_rn(t.x, y.x);
+  const float pe = __fmaf_rn(t.x, y.x, -p);
+  const float2 s = df_two_sum(x.x, p);
+  const float lo = __fadd_rn(__fadd_rn(s.y, pe), __fmaf_rn(t.x, y.y, __fmaf_rn(t.y, y.x, x.y)));
+  return df_quick_two_sum(s.x, lo);
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -p)));
+  return df_quick_two_sum(p, e);
+}
+
+// ------------------------------------------------------------------ per-precision arithmetic
+
+// Butterfly x' = x - i tau y, y' = y - i tau x (one rounding per real output).
+__device__ __forceinline__ void bfly(float2 x, float2 y, float tau, float2& xn, float2& yn) {
+  xn = make_float2(fmaf(tau, y.y, x.x), fmaf(-tau, y.x, x.y));
+  yn = make_float2(fmaf(tau, x.y, y.x), fmaf(-tau, x.x, y.y));
+}
+__device__ __forceinline__ void bfly(double2 x, double2 y, double tau, double2& xn,
+                                     double2& yn) {
+  xn = make_double2(fma(tau, y.y, x.x), fma(-tau, y.x, x.y));
+  yn = make_double2(fma(tau, x.y, y.x), fma(-tau, x.x, y.y));
+}
+__device__ __forceinline__ void bfly(float4 x, float4 y, float2 tau, float4& xn, float4& yn) {
+  // re(x') = re x + tau im y, im(x') = im x - tau re y
+  const float2 nt = df_neg(tau);
+  const float2 a = df_fma(tau, make_float2(y.z, y.w), make_float2(x.x, x.y));
+  const float2 b = df_fma(nt, make_float2(y.x, y.y), make_float2(x.z, x.w));
+  const float2 c = df_fma(tau, make_float2(x.z, x.w), make_float2(y.x, y.y));
+  const float2 d = df_fma(nt, make_float2(x.x, x.y), make_float2(y.z, y.w));
+  xn = make_float4(a.x, a.y, b.x, b.y);
+  yn = make_float4(c.x, c.y, d.x, d.y);
+}
+
+// a * b (complex)
+__device__ __forceinline__ float2 zmul(float2 a, float2 b) { return cmul(a, b); }
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ float4 zmul(float4 a, float4 b) {
+  const float2 ar = make_float2(a.x, a.y), ai = make_float2(a.z, a.w);
+  const float2 br = make_float2(b.x, b.y), bi = make_float2(b.z, b.w);
+  const float2 re = df_fma(ar, br, df_mul(df_neg(ai), bi));
+  const float2 im = df_fma(ar, bi, df_mul(ai, br));
+  return make_float4(re.x, re.y, im.x, im.y);
+}
+// acc + c * v (complex)
+__device__ __forceinline__ float2 zfma(float2 c, float2 v, float2 acc) { return cfma(c, v, acc); }
+__device__ __forceinline__ double2 zfma(double2 c, double2 v, double2 acc) {
+  return cfma(c, v, acc);
+}
+__device__ __forceinline__ float4 zfma(float4 c, float4 v, float4 acc) {
+  const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
+  const float2 vr = make_float2(v.x, v.y), vi = make_float2(v.z, v.w);
+  const float2 re = df_fma(cr, vr, df_fma(df_neg(ci), vi, make_float2(acc.x, acc.y)));
+  const float2 im = df_fma(cr, vi, df_fma(ci, vr, make_float2(acc.z, acc.w)));
+  return make_float4(re.x, re.y, im.x, im.y);
 }
 
 // ------------------------------------------------------------------ pass kernel
@@ -74,7 +221,7 @@ template <int RB> __device__ __forceinline__ int tile_elem(int t, int r, int g) 
 
 template <typename Real, int RB, bool SWAP>
 __device__ __forceinline__ void kick_registers(cplx<Real> (&v)[1 << RB], int g, int lo, int hi,
-                                               Real tau) {
+                                               scal<Real> tau) {
 #pragma unroll
   for (int b = 0; b < RB; ++b) {
     const int bit = g + b;
@@ -82,13 +229,8 @@ __device__ __forceinline__ void kick_registers(cplx<Real> (&v)[1 << RB], int g, 
 #pragma unroll
       for (int r = 0; r < (1 << RB); ++r) {
         if (r & (1 << b)) continue;
-        const cplx<Real> x = v[r];
-        const cplx<Real> y = v[r | (1 << b)];
         cplx<Real> xn, yn;
-        xn.x = fma(tau, y.y, x.x);
-        xn.y = fma(-tau, y.x, x.y);
-        yn.x = fma(tau, x.y, y.x);
-        yn.y = fma(-tau, x.x, y.y);
+        bfly(v[r], v[r | (1 << b)], tau, xn, yn);
         if (SWAP) {
           v[r] = yn;
           v[r | (1 << b)] = xn;
@@ -101,32 +243,41 @@ __device__ __forceinline__ void kick_registers(cplx<Real> (&v)[1 << RB], int g, 
   }
 }
 
-template <typename Real, int RB, int EPI, bool SWAP>
-__global__ void __launch_bounds__(512) pass_kernel(const PassArgs<Real> A) {
+// NBT > 0: the tile size 2^NBT is a compile-time constant (the large tiles of the hot path),
+// so every shared-memory index folds to a per-thread base plus a constant; NBT == 0: the
+// tile size A.NB is read at run time (small states).
+template <typename Real, int NBT, int RB, int EPI, bool SWAP>
+__global__ void __launch_bounds__(256) pass_kernel(const PassArgs<Real> A) {
   using C = cplx<Real>;
   constexpr int R = 1 << RB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
 
-  const int NB = A.NB;
+  const int NB = NBT > 0 ? NBT : A.NB;
   const int t = threadIdx.x;
   // flattened grid: blockIdx.x = vec * ntiles + tile (ntiles = 2^(L - NB))
   const int tilebits = A.L - NB;
-  const int64_t vec = (int64_t)blockIdx.x >> tilebits;
-  const int64_t cta = (int64_t)blockIdx.x & ((int64_t(1) << tilebits) - 1);
-  const int64_t mid = cta & ((int64_t(1) << A.midbits) - 1);
-  const int64_t top = cta >> A.midbits;
-  const int64_t base = (mid << A.c) | (top << A.topshift);
-  const int cmask = (1 << A.c) - 1;
-  auto gidx = [&](int e) -> int64_t {
-    return base | (int64_t)(e & cmask) | ((int64_t)(e >> A.c) << A.start);
-  };
+  const int64_t vec = (int64_t)(blockIdx.x >> tilebits);
+  const uint32_t cta = blockIdx.x & ((1u << tilebits) - 1u);
+  const uint32_t mid = cta & ((1u << A.midbits) - 1u);
+  const uint32_t top = cta >> A.midbits;
+  const int c = A.c, start = A.start;
+  const uint32_t cmask = (1u << c) - 1u;
+  // global index of element e = t | (r << g_top): tbase + roff[r] (t and r bits are disjoint)
+  const int g_top = NB - RB;
+  const uint32_t tb = (uint32_t)t;
+  const uint32_t tbase = ((mid << c) | (top << A.topshift)) + (tb & cmask) + ((tb >> c) << start);
+  uint32_t roff[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t er = (uint32_t)r << g_top;
+    roff[r] = (er & cmask) + ((er >> c) << start);
+  }
 
   const C* __restrict__ src = A.src + vec * A.d;
   C v[R];
-  const int g_top = NB - RB;
 #pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = src[gidx(tile_elem<RB>(t, r, g_top))];
+  for (int r = 0; r < R; ++r) v[r] = src[tbase + roff[r]];
 
   // Round 0: register bits are the top RB tile bits.
   int hi = NB;
@@ -159,84 +310,90 @@ __global__ void __launch_bounds__(512) pass_kernel(const PassArgs<Real> A) {
   C* __restrict__ dst = A.dst + vec * A.d;
   if (EPI == EPI_STORE) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[gidx(tile_elem<RB>(t, r, g_top))] = v[r];
+    for (int r = 0; r < R; ++r) dst[tbase + roff[r]] = v[r];
     return;
   }
   const int64_t prob = vec / A.vec_per_prob;
   const C* __restrict__ tlo = A.tab_lo + prob * A.tab_lo_stride;
   const C* __restrict__ thi = A.tab_hi + prob * A.tab_hi_stride;
-  const int64_t lomask = (int64_t(1) << A.a) - 1;
-  C cj = mk<C>(0, 0);
+  const uint32_t lomask = (1u << A.a) - 1u;
+  const int am1 = A.a - 1;
+  C cj;
   if (EPI == EPI_PHASE_ACC) cj = A.coef[vec * A.coef_stride + A.jstep];
   if (EPI == EPI_PHASE_HORNER) cj = A.coef[vec * A.coef_stride];
   C* __restrict__ acc = A.acc + vec * A.d;
   const C* __restrict__ pin = A.psi_in + vec * A.d;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const int64_t s = gidx(tile_elem<RB>(t, r, g_top));
-    const C p = cmul(__ldg(&tlo[s & lomask]), __ldg(&thi[((s >> (A.a - 1)) << 1) | (s & 1)]));
-    const C val = cmul(p, v[r]);
+    const uint32_t s = tbase + roff[r];
+    const C p = zmul(__ldg(&tlo[s & lomask]), __ldg(&thi[((s >> am1) << 1) | (s & 1u)]));
+    const C val = zmul(p, v[r]);
     if (EPI == EPI_PHASE) {
       dst[s] = val;
     } else if (EPI == EPI_PHASE_ACC) {
       dst[s] = val;
-      acc[s] = cfma(cj, val, acc[s]);
+      acc[s] = zfma(cj, val, acc[s]);
     } else {  // Horner: dst (= acc) = psi_in + z * U acc
-      dst[s] = cfma(cj, val, pin[s]);
+      dst[s] = zfma(cj, val, pin[s]);
     }
   }
 }
 
-template <typename Real, int RB, int EPI, bool SWAP>
+template <typename Real, int NBT, int RB, int EPI, bool SWAP>
 static int launch_pass_t(const PassArgs<Real>& a, int nvec, cudaStream_t st) {
   const int threads = 1 << (a.NB - RB);
-  const size_t smem = (size_t)((1 << a.NB) + (1 << (a.NB - RB))) * sizeof(cplx<Real>);
   // at most (2^12 + 2^8) * 8 or (2^11 + 2^8) * 16 bytes: below the 48 KiB default
+  const size_t smem = (size_t)((1 << a.NB) + (1 << (a.NB - RB))) * sizeof(cplx<Real>);
   const int64_t ntiles = (int64_t)1 << (a.L - a.NB);
   if (ntiles * nvec > 0x7fffffffLL) {
     set_error("launch_pass: grid too large (nvec %d, tiles %lld)", nvec, (long long)ntiles);
     return FLOQUET_EINVAL;
   }
   dim3 grid((unsigned)(ntiles * nvec));
-  pass_kernel<Real, RB, EPI, SWAP><<<grid, threads, smem, st>>>(a);
+  pass_kernel<Real, NBT, RB, EPI, SWAP><<<grid, threads, smem, st>>>(a);
   count_launch();
   FQ_CHECK_LAUNCH();
   return FLOQUET_OK;
 }
 
-template <typename Real, int RB>
+template <typename Real, int NBT, int RB>
 static int dispatch_epi(const PassArgs<Real>& a, int epi, bool swap, int nvec, cudaStream_t st) {
   switch (epi * 2 + (swap ? 1 : 0)) {
-    case 0: return launch_pass_t<Real, RB, EPI_STORE, false>(a, nvec, st);
-    case 1: return launch_pass_t<Real, RB, EPI_STORE, true>(a, nvec, st);
-    case 2: return launch_pass_t<Real, RB, EPI_PHASE, false>(a, nvec, st);
-    case 3: return launch_pass_t<Real, RB, EPI_PHASE, true>(a, nvec, st);
-    case 4: return launch_pass_t<Real, RB, EPI_PHASE_ACC, false>(a, nvec, st);
-    case 5: return launch_pass_t<Real, RB, EPI_PHASE_ACC, true>(a, nvec, st);
-    case 6: return launch_pass_t<Real, RB, EPI_PHASE_HORNER, false>(a, nvec, st);
-    case 7: return launch_pass_t<Real, RB, EPI_PHASE_HORNER, true>(a, nvec, st);
+    case 0: return launch_pass_t<Real, NBT, RB, EPI_STORE, false>(a, nvec, st);
+    case 1: return launch_pass_t<Real, NBT, RB, EPI_STORE, true>(a, nvec, st);
+    case 2: return launch_pass_t<Real, NBT, RB, EPI_PHASE, false>(a, nvec, st);
+    case 3: return launch_pass_t<Real, NBT, RB, EPI_PHASE, true>(a, nvec, st);
+    case 4: return launch_pass_t<Real, NBT, RB, EPI_PHASE_ACC, false>(a, nvec, st);
+    case 5: return launch_pass_t<Real, NBT, RB, EPI_PHASE_ACC, true>(a, nvec, st);
+    case 6: return launch_pass_t<Real, NBT, RB, EPI_PHASE_HORNER, false>(a, nvec, st);
+    case 7: return launch_pass_t<Real, NBT, RB, EPI_PHASE_HORNER, true>(a, nvec, st);
   }
   set_error("launch_pass: bad epilogue %d", epi);
   return FLOQUET_EINVAL;
 }
 
-// Register bits per thread: 16 complex64 or 8 complex128 (32 registers of data either
-// way); smaller tiles use fewer so that a tile always has at least one thread per group.
-template <typename Real> static int reg_bits(int NB);
-template <> int reg_bits<float>(int NB) { return NB >= 4 ? 4 : 3; }
-template <> int reg_bits<double>(int NB) { return 3; }
+// Largest tile (bits) per precision: 2^12 complex64 (34 KiB of shared memory with padding),
+// 2^11 complex128 or double-float (36 KiB).
+template <typename Real> static constexpr int max_tile_bits() { return 11; }
+template <> constexpr int max_tile_bits<float>() { return 12; }
 
+// Register bits per thread: 16 complex64 or 8 complex128 / double-float complex (32
+// registers of data either way); a tile smaller than 2^4 complex64 uses 3.
 template <typename Real>
 int launch_pass(const PassArgs<Real>& a, int epi, bool swap, int nvec, cudaStream_t st) {
-  const int rb = reg_bits<Real>(a.NB);
-  if (rb == 4) return dispatch_epi<Real, 4>(a, epi, swap, nvec, st);
-  return dispatch_epi<Real, 3>(a, epi, swap, nvec, st);
-}
-template <> int launch_pass<double>(const PassArgs<double>& a, int epi, bool swap, int nvec,
-                                    cudaStream_t st) {
-  return dispatch_epi<double, 3>(a, epi, swap, nvec, st);
+  constexpr int NBM = max_tile_bits<Real>();
+  if constexpr (std::is_same<Real, float>::value) {
+    if (a.NB == NBM) return dispatch_epi<Real, NBM, 4>(a, epi, swap, nvec, st);
+    if (a.NB >= 4) return dispatch_epi<Real, 0, 4>(a, epi, swap, nvec, st);
+    return dispatch_epi<Real, 0, 3>(a, epi, swap, nvec, st);
+  } else {
+    if (a.NB == NBM) return dispatch_epi<Real, NBM, 3>(a, epi, swap, nvec, st);
+    return dispatch_epi<Real, 0, 3>(a, epi, swap, nvec, st);
+  }
 }
 template int launch_pass<float>(const PassArgs<float>&, int, bool, int, cudaStream_t);
+template int launch_pass<double>(const PassArgs<double>&, int, bool, int, cudaStream_t);
+template int launch_pass<dfloat>(const PassArgs<dfloat>&, int, bool, int, cudaStream_t);
 
 // ------------------------------------------------------------------ elementwise kernels
 
@@ -244,10 +401,8 @@ template <typename Rin, typename Rout>
 __global__ void convert_kernel(const cplx<Rin>* __restrict__ in, cplx<Rout>* __restrict__ out,
                                int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const cplx<Rin> x = in[i];
-    out[i] = mk<cplx<Rout>>((Rout)x.x, (Rout)x.y);
-  }
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = from_d2<Rout>(to_d2(in[i]));
 }
 
 static unsigned grid_for(int64_t n, int threads) {
@@ -268,6 +423,8 @@ template int launch_convert<double, float>(const double2*, float2*, int64_t, cud
 template int launch_convert<float, double>(const float2*, double2*, int64_t, cudaStream_t);
 template int launch_convert<double, double>(const double2*, double2*, int64_t, cudaStream_t);
 template int launch_convert<float, float>(const float2*, float2*, int64_t, cudaStream_t);
+template int launch_convert<double, dfloat>(const double2*, float4*, int64_t, cudaStream_t);
+template int launch_convert<dfloat, double>(const float4*, double2*, int64_t, cudaStream_t);
 
 template <typename Rin, typename Rout>
 __global__ void filter_init_kernel(const cplx<Rin>* __restrict__ in, int64_t in_stride,
@@ -275,13 +432,12 @@ __global__ void filter_init_kernel(const cplx<Rin>* __restrict__ in, int64_t in_
                                    const cplx<Rout>* __restrict__ coef, int64_t coef_stride,
                                    int64_t d) {
   const int64_t vec = blockIdx.y;
-  const cplx<Rout> c0 = coef ? coef[vec * coef_stride] : mk<cplx<Rout>>(1, 0);
+  const double2 c0 = coef ? to_d2(coef[vec * coef_stride]) : make_double2(1, 0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const cplx<Rin> x = in[vec * in_stride + i];
-    const cplx<Rout> y = mk<cplx<Rout>>((Rout)x.x, (Rout)x.y);
-    if (work) work[vec * d + i] = y;
-    acc[vec * d + i] = cmul(c0, y);
+    const double2 x = to_d2(in[vec * in_stride + i]);
+    if (work) work[vec * d + i] = from_d2<Rout>(x);
+    acc[vec * d + i] = from_d2<Rout>(cmul(c0, x));
   }
 }
 
@@ -306,6 +462,9 @@ template int launch_filter_init<double, double>(const double2*, int64_t, double2
                                                 cudaStream_t);
 template int launch_filter_init<float, float>(const float2*, int64_t, float2*, float2*,
                                               const float2*, int64_t, int64_t, int, cudaStream_t);
+template int launch_filter_init<double, dfloat>(const double2*, int64_t, float4*, float4*,
+                                                const float4*, int64_t, int64_t, int,
+                                                cudaStream_t);
 
 // out[vec * out_stride + i] = in[vec * d + i] (converted)
 template <typename Rin, typename Rout>
@@ -315,8 +474,7 @@ __global__ void convert_strided_kernel(const cplx<Rin>* __restrict__ in,
   const int64_t vec = blockIdx.y;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const cplx<Rin> x = in[vec * d + i];
-    out[vec * out_stride + i] = mk<cplx<Rout>>((Rout)x.x, (Rout)x.y);
+    out[vec * out_stride + i] = from_d2<Rout>(to_d2(in[vec * d + i]));
   }
 }
 
@@ -333,11 +491,6 @@ static int launch_convert_strided(const cplx<Rin>* in, cplx<Rout>* out, int64_t 
 
 // ------------------------------------------------------------------ operator set-up
 
-// Largest tile (bits) per precision: 2^12 complex64 (34 KiB of shared memory with padding),
-// 2^11 complex128 (36 KiB).
-template <typename Real> static int max_tile_bits();
-template <> int max_tile_bits<float>() { return 12; }
-template <> int max_tile_bits<double>() { return 11; }
 
 // Split the L qubits into passes: the first kicks the NB lowest qubits in contiguous tiles;
 // each later pass keeps at least `min_cols` low (contiguous) bits in its tile for coalescing
@@ -376,7 +529,7 @@ static PassArgs<Real> make_args(const floquet_op* op, const Pass& ps, const cplx
     a.midbits = 0;
     a.topshift = op->L;
   }
-  a.tau = (Real)op->tau;
+  a.tau = scal_from<Real>(op->tau);
   a.tab_lo = tlo;
   a.tab_hi = thi;
   a.a = op->tabs.a;
@@ -445,6 +598,13 @@ int op_init(floquet_op* op, int L, double J, double g, const double* h, int npro
       hi[p * T.hi_n + y] = mk<double2>(cos(th), -sin(th));
     }
   }
+  std::vector<float4> lodf(lo.size()), hidf(hi.size());
+  for (size_t i = 0; i < lo.size(); ++i) lodf[i] = from_d2<dfloat>(lo[i]);
+  for (size_t i = 0; i < hi.size(); ++i) hidf[i] = from_d2<dfloat>(hi[i]);
+  FQ_CUDA(cudaMalloc(&T.lodf, lo.size() * sizeof(float4)));
+  FQ_CUDA(cudaMalloc(&T.hidf, hi.size() * sizeof(float4)));
+  FQ_CUDA(cudaMemcpy(T.lodf, lodf.data(), lo.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  FQ_CUDA(cudaMemcpy(T.hidf, hidf.data(), hi.size() * sizeof(float4), cudaMemcpyHostToDevice));
   for (size_t i = 0; i < lo.size(); ++i) lo32[i] = mk<float2>((float)lo[i].x, (float)lo[i].y);
   for (size_t i = 0; i < hi.size(); ++i) hi32[i] = mk<float2>((float)hi[i].x, (float)hi[i].y);
   FQ_CUDA(cudaMalloc(&T.lo64, lo.size() * sizeof(double2)));
@@ -473,6 +633,8 @@ void op_free(floquet_op* op) {
   cudaFree(op->tabs.lo64);
   cudaFree(op->tabs.hi64);
   cudaFree(op->tabs.lo32);
+  cudaFree(op->tabs.lodf);
+  cudaFree(op->tabs.hidf);
   cudaFree(op->tabs.hi32);
   cudaFree(op->work);
   cudaFree(op->acc);
@@ -480,15 +642,23 @@ void op_free(floquet_op* op) {
   cudaFree(op->coef);
 }
 
+template <typename Real> static int sweep_dtype();
+template <> int sweep_dtype<float>() { return FLOQUET_C64; }
+template <> int sweep_dtype<double>() { return FLOQUET_C128; }
+template <> int sweep_dtype<dfloat>() { return FLOQUET_C128_DF; }
+
 template <typename Real> static const Plan& plan_of(const floquet_op* op);
 template <> const Plan& plan_of<float>(const floquet_op* op) { return op->plan32; }
 template <> const Plan& plan_of<double>(const floquet_op* op) { return op->plan64; }
+template <> const Plan& plan_of<dfloat>(const floquet_op* op) { return op->plan64; }
 template <typename Real> static const cplx<Real>* tlo_of(const floquet_op* op);
 template <> const float2* tlo_of<float>(const floquet_op* op) { return op->tabs.lo32; }
 template <> const double2* tlo_of<double>(const floquet_op* op) { return op->tabs.lo64; }
+template <> const float4* tlo_of<dfloat>(const floquet_op* op) { return op->tabs.lodf; }
 template <typename Real> static const cplx<Real>* thi_of(const floquet_op* op);
 template <> const float2* thi_of<float>(const floquet_op* op) { return op->tabs.hi32; }
 template <> const double2* thi_of<double>(const floquet_op* op) { return op->tabs.hi64; }
+template <> const float4* thi_of<dfloat>(const floquet_op* op) { return op->tabs.hidf; }
 
 // One U application (all passes) from `in` to `out` (in place allowed), with the last
 // pass's epilogue `epi`.
@@ -524,6 +694,7 @@ int apply_u(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int nvec, int
 }
 template int apply_u<float>(floquet_op*, const float2*, float2*, int, int, cudaStream_t);
 template int apply_u<double>(floquet_op*, const double2*, double2*, int, int, cudaStream_t);
+template int apply_u<dfloat>(floquet_op*, const float4*, float4*, int, int, cudaStream_t);
 
 // ------------------------------------------------------------------ filter loops
 
@@ -561,7 +732,17 @@ template <typename F>
 static int run_loop(floquet_op* op, bool use_graph, int64_t k, int nvec, int dtype, int form,
                     const void* coef, int vpp, int64_t launches_per_body, cudaStream_t st,
                     F body) {
-  if (!use_graph) return body(st);
+  const int kind = dtype == FLOQUET_C64 ? 1 : (dtype == FLOQUET_C128 ? 0 : 2);
+  const double b = dtype == FLOQUET_C64 ? 8.0 : 16.0;
+  const int64_t u_apps = (k - 1) * (int64_t)nvec;
+  const double alg_bytes = (form == FLOQUET_FORM_ACC ? 4.0 : 3.0) * b * (double)op->d * u_apps;
+  if (!use_graph) {
+    cudaEvent_t a;
+    const bool prof = profile_begin(st, &a);
+    const int rc = body(st);
+    if (prof) profile_end(st, a, kind, u_apps, alg_bytes);
+    return rc;
+  }
   if (!op->cap_stream) {
     FQ_CUDA(cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking));
     FQ_CUDA(cudaEventCreateWithFlags(&op->ev_in, cudaEventDisableTiming));
@@ -603,7 +784,10 @@ static int run_loop(floquet_op* op, bool use_graph, int64_t k, int nvec, int dty
   }
   FQ_CUDA(cudaEventRecord(op->ev_in, st));
   FQ_CUDA(cudaStreamWaitEvent(cs, op->ev_in, 0));
+  cudaEvent_t pa;
+  const bool prof = profile_begin(cs, &pa);
   FQ_CUDA(cudaGraphLaunch(g->exec, cs));
+  if (prof) profile_end(cs, pa, kind, u_apps, alg_bytes);
   FQ_CUDA(cudaEventRecord(op->ev_out, cs));
   FQ_CUDA(cudaStreamWaitEvent(st, op->ev_out, 0));
   count_launch(launches_per_body);
@@ -628,7 +812,7 @@ int filter_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio
     return FLOQUET_OK;
   };
   if (k > 1)
-    FQ_TRY(run_loop(op, use_graph, k, nvec, sizeof(Real) == 4 ? FLOQUET_C64 : FLOQUET_C128,
+    FQ_TRY(run_loop(op, use_graph, k, nvec, sweep_dtype<Real>(),
                     FLOQUET_FORM_ACC, coef, vec_per_prob, (k - 1) * np, st, body));
   return launch_convert_strided<Real, Rio>(acc, out, out_stride, d, nvec, st);
 }
@@ -651,7 +835,7 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
     return FLOQUET_OK;
   };
   if (k > 1)
-    FQ_TRY(run_loop(op, use_graph, k, nvec, sizeof(Real) == 4 ? FLOQUET_C64 : FLOQUET_C128,
+    FQ_TRY(run_loop(op, use_graph, k, nvec, sweep_dtype<Real>(),
                     FLOQUET_FORM_HORNER, zs, vec_per_prob, (k - 1) * np, st, body));
   return launch_convert_strided<Real, Rio>(acc, out, out_stride, d, nvec, st);
 }
@@ -665,5 +849,6 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
 FQ_INST_FILTER(float, float)
 FQ_INST_FILTER(float, double)
 FQ_INST_FILTER(double, double)
+FQ_INST_FILTER(dfloat, double)
 
 }  // namespace fq

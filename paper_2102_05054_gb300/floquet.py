@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfloquet.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT = 0, -1, -2, -3, -4, -5
-C128, C64 = 0, 1
-FP64, FILTER_FP32 = 0, 1
+C128, C64, C128_DF = 0, 1, 2
+FP64, FILTER_FP32, FILTER_DF = 0, 1, 2
 FORM_ACC, FORM_HORNER = 0, 1
 
 _lib = None
@@ -43,6 +43,8 @@ SIGNATURES = {
     "arnoldi_eigs_batched": (_c_int, [_c_int, _c_double, _c_double, _dptr, _c_int, _dptr, _c_int,
                                       _c_int64, _c_int, _c_int, _c_double, _c_double, _c_int,
                                       _c_void_p, _dptr, _dptr, _iptr, _c_void_p]),
+    "floquet_profile_enable": (_c_int, [_c_int]),
+    "floquet_profile_read": (_c_int, [_dptr, ctypes.POINTER(_c_int64), _dptr]),
     "floquet_launch_count": (_c_int64, []),
     "floquet_reset_launch_count": (None, []),
     "floquet_last_error": (ctypes.c_char_p, []),
@@ -157,16 +159,19 @@ class Floquet:
             raise ValueError("tensor size must be a multiple of d")
         return n // self.d
 
-    def apply_u(self, psi_in, psi_out, stream=None):
+    def apply_u(self, psi_in, psi_out, stream=None, sweep=None):
+        """sweep=C128_DF runs complex128 states through double-float sweeps."""
+        dt = _dtype_code(psi_in) if sweep is None else sweep
         _check(lib().floquet_apply_u(self.handle, _ptr(psi_in), _ptr(psi_out),
-                                     self._nvec(psi_in), _dtype_code(psi_in), _stream(stream)),
+                                     self._nvec(psi_in), dt, _stream(stream)),
                "floquet_apply_u")
         return psi_out
 
-    def filter_apply(self, phi, k, psi_in, psi_out, form=FORM_ACC, stream=None):
+    def filter_apply(self, phi, k, psi_in, psi_out, form=FORM_ACC, stream=None, sweep=None):
+        dt = _dtype_code(psi_in) if sweep is None else sweep
         _check(lib().filter_apply(self.handle, float(phi), int(k), _ptr(psi_in), _ptr(psi_out),
-                                  self._nvec(psi_in), _dtype_code(psi_in), int(form),
-                                  _stream(stream)), "filter_apply")
+                                  self._nvec(psi_in), dt, int(form), _stream(stream)),
+               "filter_apply")
         return psi_out
 
     def ritz_residuals(self, X, stream=None):
@@ -224,6 +229,20 @@ def arnoldi_eigs_batched(L, J, g, hs, phis, k, nev, m, v0, tol=0.0, tol_resid=0.
         raise FloquetError(rc, "arnoldi_eigs_batched")
     om = (ev[0::2] + 1j * ev[1::2]).reshape(R, P, nev)
     return om, res.reshape(R, P, nev), nconv.reshape(R, P), rc
+
+
+def profile_enable(on=True):
+    _check(lib().floquet_profile_enable(1 if on else 0), "floquet_profile_enable")
+
+
+def profile_read():
+    """{'c128'|'c64'|'df': (sweep_ms, u_applications, algorithmic_bytes)} since enable."""
+    ms = np.zeros(3)
+    apps = (ctypes.c_int64 * 3)()
+    by = np.zeros(3)
+    _check(lib().floquet_profile_read(_dp(ms), apps, _dp(by)), "floquet_profile_read")
+    return {"c128": (ms[0], apps[0], by[0]), "c64": (ms[1], apps[1], by[1]),
+            "df": (ms[2], apps[2], by[2])}
 
 
 def launch_count():

@@ -173,3 +173,18 @@ def test_arnoldi_eigs_batched_matches_dense():
             assert res[r, p].max() < 1e-10
             assert nconv[r, p] == nev
     _ = torch
+
+
+def test_arnoldi_eigs_double_float_form_L12():
+    om, res, nconv, rc, X, op = _solve(12, 1.0, 0.9045, 1.0, 2, 0.0, 128, 24, 96, precision=2)
+    assert rc == 0 and nconv == 24
+    _check_against_dense(om, res, X, op, 0.0, 24)
+
+
+def test_arnoldi_eigs_double_float_special_case_g0_L16():
+    L, phi, k, nev, m = 16, math.pi / 3, 1024, 50, 160
+    om, res, nconv, rc, X, op = _solve(L, 1.0, 0.0, 2.0, 1, phi, k, nev, m, precision=2)
+    lam = model.spectrum_g0(L, 1.0, inputs.disorder(L, 2.0, 1))
+    want = lam[krylov.select_closest(lam, phi, nev)]
+    assert rc == 0 and nconv == nev
+    assert np.abs(om - want).max() < 1e-10

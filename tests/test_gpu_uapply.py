@@ -143,46 +143,97 @@ def test_filter_repeat_uses_cached_graph_and_is_deterministic():
     assert floquet.launch_count() == 1 + 32 + 1
 
 
-@pytest.mark.parametrize("dtype_name,tol", [("complex128", 1e-13), ("complex64", 1e-6)])
-def test_filter_full_length_L20_on_exact_eigenvectors(dtype_name, tol):
+def _g_from_phase(x, k):
+    """g_k(e^{ix}) = e^{i(k-1)x/2} sin(kx/2)/sin(x/2), evaluated from the exact phase x
+    (no cancellation near x = 0, unlike (1 - w^k)/(1 - w) from a rounded w)."""
+    x = math.remainder(x, 2 * math.pi)
+    if abs(x) < 1e-300:
+        return complex(k)
+    return np.exp(0.5j * (k - 1) * x) * math.sin(0.5 * k * x) / math.sin(0.5 * x)
+
+
+@pytest.mark.parametrize("dtype_name", ["complex128", "complex64"])
+def test_filter_full_length_L20_on_exact_eigenvectors(dtype_name):
     # L = 20, k = 16384 (the large workload's filter) on exact eigenvectors from closed-form
-    # special cases: g = 0 (basis states) and J = 0 (product states). g_k(U) v = g_k(w) v with
-    # the closed form of Eq. geo2 (k-term reading).
+    # special cases: g = 0 (basis states, eigenphase -theta_s) and J = 0 (product states).
+    # Bound: each U application is exact up to a relative rounding eps = (L + 3) u, and on an
+    # eigenvector that rounding is coherent (the same perturbed eigenvalue every step), so the
+    # filter output can drift by up to ~ k^2 eps / 2 in absolute terms. complex128: checked
+    # against that bound. complex64: that bound is a few percent of |g| at this k, so the
+    # check is on what the sweeps must keep: the output is parallel to the eigenvector.
     torch = require_gpu()
     from paper_2102_05054_gb300 import floquet
     dt = getattr(torch, dtype_name)
     L, k, phi = 20, 16384, 0.0
     d = 1 << L
-    # g = 0: basis state |s>
+    u = 1.1e-16 if dtype_name == "complex128" else 6e-8
+    eps = (L + 3) * u
+
+    def check(fq, v, x):
+        t_in = to_dev(v, dt)
+        t_out = torch.empty_like(t_in)
+        fq.filter_apply(phi, k, t_in, t_out)
+        torch.cuda.synchronize()
+        out = from_dev(t_out)
+        g = _g_from_phase(x, k)
+        along = np.vdot(v, out)
+        perp = np.linalg.norm(out - along * v)
+        if dtype_name == "complex128":
+            assert np.linalg.norm(out - g * v) < k * k * eps
+            assert perp < 1e-10 * abs(g)
+        else:
+            # random rounding adds ~ k * eps absolute off the eigenvector direction
+            assert perp < k * eps
+            assert abs(along - g) < 0.5 * k * eps * k
+
+    # g = 0: basis state |s>, U|s> = exp(-i theta_s)|s>
     h = inputs.disorder(L, 1.0, 1)
+    theta = model.diagonal_phases(L, 1.0, h)
     fq = floquet.Floquet(L, 1.0, 0.0, h)
-    lam = model.spectrum_g0(L, 1.0, h)
-    s = int(np.argmin(np.abs(np.angle(lam))))  # closest to the target: largest |g_k|
+    s = int(np.argmin(np.abs(np.remainder(-theta - phi + np.pi, 2 * np.pi) - np.pi)))
     e = np.zeros(d, dtype=np.complex128)
     e[s] = 1.0
-    t_in = to_dev(e, dt)
-    t_out = torch.empty_like(t_in)
-    fq.filter_apply(phi, k, t_in, t_out)
-    torch.cuda.synchronize()
-    want = geosum.gk_closed(lam[s:s + 1], phi, k)[0] * e
-    # absolute error per unit-norm input: at most ~k times one application's rounding
-    assert np.linalg.norm(from_dev(t_out) - want) < tol * k
-    # J = 0: product of single-site eigenvectors
+    check(fq, e, -theta[s] - phi)
+    # J = 0: product of single-site eigenvectors; the eigenphase is the sum of site phases
     g = 0.9045
     fq = floquet.Floquet(L, 0.0, g, h)
     X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
     v = np.ones(1, dtype=np.complex128)
-    lam_v = 1.0 + 0j
+    x = 0.0
     for i in range(L):
-        u = np.diag([np.exp(-1j * h[i]), np.exp(1j * h[i])]) @ (np.cos(g) * np.eye(2)
-                                                                - 1j * np.sin(g) * X)
-        w, vecs = np.linalg.eig(u)
+        u1 = np.diag([np.exp(-1j * h[i]), np.exp(1j * h[i])]) @ (np.cos(g) * np.eye(2)
+                                                                 - 1j * np.sin(g) * X)
+        w, vecs = np.linalg.eig(u1)
         j = int(np.argmin(np.abs(np.angle(w))))
-        v = np.kron(vecs[:, j], v)  # qubit i on the higher bits of the kron
-        lam_v *= w[j]
-    t_in = to_dev(v, dt)
+        v = np.kron(vecs[:, j] / np.linalg.norm(vecs[:, j]), v)  # qubit i on the higher bits
+        x += float(np.angle(w[j]))
+    check(fq, v, x - phi)
+
+
+@pytest.mark.parametrize("L", [3, 5, 10, 11, 12, 16, 20])
+def test_apply_u_double_float_sweeps_match_oracle(L):
+    # double-float sweeps: ~48-bit significands, so ~(L + 3) * 2^-47 relative per application
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    fq, op = _make(L, 1.0, 0.9045, 1.0, 600 + L)
+    X = inputs.random_states(1 << L, 2, 12)
+    t_in = to_dev(X, torch.complex128)
     t_out = torch.empty_like(t_in)
-    fq.filter_apply(phi, k, t_in, t_out)
+    fq.apply_u(t_in, t_out, sweep=floquet.C128_DF)
     torch.cuda.synchronize()
-    want = geosum.gk_closed(np.array([lam_v]), phi, k)[0] * v
-    assert np.linalg.norm(from_dev(t_out) - want) < tol * k
+    assert _rel(from_dev(t_out, 1 << L), op.apply_u_block(X)) < 1e-14 * (L + 3)
+
+
+@pytest.mark.parametrize("L,k,phi,form", [(10, 64, 0.0, 0), (12, 200, 1.0, 0), (13, 50, 0.4, 1),
+                                          (16, 40, math.pi / 3, 0)])
+def test_filter_double_float_matches_oracle(L, k, phi, form):
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    fq, op = _make(L, 1.0, 0.9045, 1.0, 700 + L)
+    x = inputs.complex_gaussian(1 << L, 13)
+    t_in = to_dev(x, torch.complex128)
+    t_out = torch.empty_like(t_in)
+    fq.filter_apply(phi, k, t_in, t_out, form=form, sweep=floquet.C128_DF)
+    torch.cuda.synchronize()
+    want = geosum.filter_acc(op, x, phi, k)
+    assert _rel(from_dev(t_out), want) < 1e-14 * k * (L + 3)
