@@ -509,7 +509,13 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
     FQ_CUDA(cudaStreamSynchronize(st));
     std::vector<cd> om(nb);
     for (int i = 0; i < nb; ++i) om[i] = cd(rq_h[3 * i], rq_h[3 * i + 1]);
-    const std::vector<int> sel = select_closest(om, phi, k, nev, false);
+    // Rayleigh-Ritz over [X, Y] also yields values inside the unit disk (mixtures of the
+    // correction directions); only values on the circle (eigenvalues of a unitary) inside
+    // the main lobe are candidates.
+    std::vector<cd> om_c(nb);
+    for (int i = 0; i < nb; ++i)
+      om_c[i] = std::fabs(std::abs(om[i]) - 1.0) < 1e-4 ? om[i] : cd(0.0, 0.0);
+    const std::vector<int> sel = select_closest(om_c, phi, k, nev, true);
     double worst = 0;
     for (int i : sel) worst = std::max(worst, rq_h[3 * i + 2]);
     omega_out.clear();
