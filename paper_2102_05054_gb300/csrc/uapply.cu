@@ -274,10 +274,26 @@ __global__ void __launch_bounds__(256) pass_kernel(const PassArgs<Real> A) {
     roff[r] = (er & cmask) + ((er >> c) << start);
   }
 
+  // Programmatic dependent launch: let the next pass be scheduled now (it waits for this
+  // grid's completion before touching memory), then wait for the previous pass.
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
   const C* __restrict__ src = A.src + vec * A.d;
   C v[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = src[tbase + roff[r]];
+  // For complex64 (latency bound) the epilogue's other operand, the accumulator or Horner's
+  // psi_in, is loaded together with the state so that its latency overlaps the kicks; the
+  // wider types are arithmetic bound and keep their registers for the sweep instead.
+  constexpr bool kPrefetch =
+      (EPI == EPI_PHASE_ACC || EPI == EPI_PHASE_HORNER) && sizeof(C) == 8;
+  const C* __restrict__ other = (EPI == EPI_PHASE_ACC ? A.acc : A.psi_in) + vec * A.d;
+  C pre[kPrefetch ? R : 1];
+  if (kPrefetch) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) pre[r] = other[tbase + roff[r]];
+  }
 
   // Round 0: register bits are the top RB tile bits.
   int hi = NB;
@@ -322,7 +338,6 @@ __global__ void __launch_bounds__(256) pass_kernel(const PassArgs<Real> A) {
   if (EPI == EPI_PHASE_ACC) cj = A.coef[vec * A.coef_stride + A.jstep];
   if (EPI == EPI_PHASE_HORNER) cj = A.coef[vec * A.coef_stride];
   C* __restrict__ acc = A.acc + vec * A.d;
-  const C* __restrict__ pin = A.psi_in + vec * A.d;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const uint32_t s = tbase + roff[r];
@@ -330,11 +345,14 @@ __global__ void __launch_bounds__(256) pass_kernel(const PassArgs<Real> A) {
     const C val = zmul(p, v[r]);
     if (EPI == EPI_PHASE) {
       dst[s] = val;
-    } else if (EPI == EPI_PHASE_ACC) {
-      dst[s] = val;
-      acc[s] = zfma(cj, val, acc[s]);
-    } else {  // Horner: dst (= acc) = psi_in + z * U acc
-      dst[s] = zfma(cj, val, pin[s]);
+    } else {
+      const C o = kPrefetch ? pre[kPrefetch ? r : 0] : other[s];
+      if (EPI == EPI_PHASE_ACC) {
+        dst[s] = val;
+        acc[s] = zfma(cj, val, o);
+      } else {  // Horner: dst (= acc) = psi_in + z * U acc
+        dst[s] = zfma(cj, val, o);
+      }
     }
   }
 }
@@ -349,8 +367,17 @@ static int launch_pass_t(const PassArgs<Real>& a, int nvec, cudaStream_t st) {
     set_error("launch_pass: grid too large (nvec %d, tiles %lld)", nvec, (long long)ntiles);
     return FLOQUET_EINVAL;
   }
-  dim3 grid((unsigned)(ntiles * nvec));
-  pass_kernel<Real, NBT, RB, EPI, SWAP><<<grid, threads, smem, st>>>(a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ntiles * nvec));
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  FQ_CUDA(cudaLaunchKernelEx(&cfg, pass_kernel<Real, NBT, RB, EPI, SWAP>, a));
   count_launch();
   FQ_CHECK_LAUNCH();
   return FLOQUET_OK;
