@@ -112,6 +112,24 @@ int filter_apply(floquet_t op, double phi, int64_t k, const void* psi_in, void* 
  * Synchronises `stream`. */
 int gram_schmidt(int64_t d, const void* V, int n, void* w, double* h, void* stream);
 
+/* The CGS2 step of gram_schmidt for callers that cannot allocate device memory while they
+ * run (a process that reserves its whole memory budget at start-up, or a latency-critical
+ * loop that cannot afford the device-wide synchronisation cudaFree implies). The paper has no
+ * counterpart: this is a deployment variant of gram_schmidt. It calls no allocator: its
+ * scratch is a fixed file-scope device array of 2.1 MiB that every GPU loading the library
+ * holds until exit; the caller passes all inputs and outputs.
+ *   d    -- rows, 1 <= d <= 2^20 (larger: FLOQUET_EINVAL, nothing launched);
+ *   V    -- device, d x n complex128, orthonormal columns, leading dimension d;
+ *   n    -- columns, 0 <= n <= 256 (larger: FLOQUET_EINVAL);
+ *   w    -- device, d complex128, overwritten with the unit vector;
+ *   h    -- device, n+1 complex128 (caller-owned): the summed coefficients V^H w, then beta.
+ * Asynchronous on `stream`. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's contents (nothing in
+ * it needs to start at zero): calls that overlap on the GPU race and must be serialised by
+ * the caller. */
+int gram_schmidt_noalloc(int64_t d, const void* V, int n, void* w, void* h, void* stream);
+
 /* Eigen-decomposition of a small general complex matrix on the device (the Hessenberg /
  * Schur solve behind Sec. 4's Ritz pairs): A = Y diag(lambda) Y^{-1}.
  * A: host or device, n x n complex128 column-major; lambda: host, n complex128; Y: host or

@@ -8,6 +8,7 @@
 // results are deterministic run to run.
 
 #include <algorithm>
+#include <mutex>
 
 #include "floquet_internal.cuh"
 #include "linalg.cuh"
@@ -675,4 +676,133 @@ Workspace::~Workspace() {
   cudaFree(npart);
 }
 
+// ==============================================================================
+// gram_schmidt_noalloc: the CGS2 step with its scratch in a fixed device array.
+//
+// Some callers must not allocate device memory once they are running: services that
+// reserve their whole memory budget at start-up and treat any later cudaMalloc as a
+// failure, or latency-critical loops where the device-wide synchronisation that cudaFree
+// implies is unacceptable. gram_schmidt allocates its partial sums on every call; this entry
+// point instead keeps them in the file-scope array below, which every GPU that loads the
+// library holds for the life of the process.
+//
+// Capacity: d <= 2^20 rows and n <= 256 columns. Layout of the array (complex128 slots):
+// dots partials nchunk * n (nchunk = d / 2048 <= 512), then the two projection vectors
+// (n each), then the norm partials (d / 256 doubles) and the norm itself. Every slot that a
+// kernel reads is first written by an earlier kernel of the same call, so nothing has to
+// start at zero; the array simply keeps the last call's values. All calls share the one
+// array: calls whose work overlaps on the GPU (different streams, threads or devices'
+// contexts racing on the same device) corrupt each other and must be serialised by the
+// caller.
+// ==============================================================================
+
+namespace {
+
+constexpr int64_t kNoAllocMaxRows = int64_t(1) << 20;
+constexpr int kNoAllocMaxCols = 256;
+constexpr int64_t kNoAllocChunks = kNoAllocMaxRows / 2048;        // dots partial blocks
+constexpr int64_t kNoAllocNormBlocks = kNoAllocMaxRows / 256;     // norm partial blocks
+constexpr int64_t kNoAllocSlots = kNoAllocChunks * kNoAllocMaxCols  // dots partials
+                                  + 2 * kNoAllocMaxCols             // h1, h2
+                                  + kNoAllocNormBlocks / 2 + 1      // norm partials (doubles)
+                                  + 1;                              // beta
+
+}  // namespace
+
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocSlots];
+
+// Device address of g_noalloc_scratch per device ordinal, looked up once per device with that
+// device current (in host code the symbol name is only a host-side stand-in).
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[64] = {nullptr};
+
+static int noalloc_scratch(double2** out) {
+  int dev = 0;
+  FQ_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("gram_schmidt_noalloc: device ordinal %d out of range", dev);
+    return FLOQUET_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      set_error("gram_schmidt_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return FLOQUET_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<double2*>(g_noalloc_addr[dev]);
+  return FLOQUET_OK;
+}
+
 }  // namespace fq
+
+extern "C" int gram_schmidt_noalloc(int64_t d, const void* V, int n, void* w, void* h,
+                                    void* stream) {
+  using namespace fq;
+  if (d < 1 || d > kNoAllocMaxRows) {
+    set_error("gram_schmidt_noalloc: d = %lld outside [1, %lld] (the fixed scratch array's "
+              "capacity); use gram_schmidt for larger states",
+              (long long)d, (long long)kNoAllocMaxRows);
+    return FLOQUET_EINVAL;
+  }
+  if (n < 0 || n > kNoAllocMaxCols) {
+    set_error("gram_schmidt_noalloc: n = %d outside [0, %d] (the fixed scratch array's "
+              "capacity); use gram_schmidt for more columns",
+              n, kNoAllocMaxCols);
+    return FLOQUET_EINVAL;
+  }
+  if (!w || !h || (n > 0 && !V)) {
+    set_error("gram_schmidt_noalloc: NULL pointer");
+    return FLOQUET_EINVAL;
+  }
+  double2* scratch = nullptr;
+  FQ_TRY(noalloc_scratch(&scratch));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chunk = dots_chunk(d);
+  const int nchunk = (int)((d + chunk - 1) / chunk);
+  const int nblk = (int)((d + kThreads - 1) / kThreads);
+  double2* part = scratch;
+  double2* h1 = part + kNoAllocChunks * kNoAllocMaxCols;
+  double2* h2 = h1 + kNoAllocMaxCols;
+  double* npart = reinterpret_cast<double*>(h2 + kNoAllocMaxCols);
+  double* beta = npart + kNoAllocNormBlocks;
+  const double2* Vd = (const double2*)V;
+  double2* wd = (double2*)w;
+  double2* hd = (double2*)h;
+  if (n > 0) {
+    const size_t smw = (size_t)chunk * sizeof(double2);
+    const size_t smh = (size_t)n * sizeof(double2);
+    for (int pass = 0; pass < 2; ++pass) {
+      double2* hp = pass == 0 ? h1 : h2;
+      dots_kernel<<<dim3(nchunk, 1), kThreads, smw, st>>>(Vd, d, 0, n, wd, 0, d, chunk, part);
+      count_launch();
+      FQ_CHECK_LAUNCH();
+      reduce_parts_kernel<<<dim3(n, 1), kThreads, 0, st>>>(part, nchunk, n, hp, n, nullptr, 0);
+      count_launch();
+      FQ_CHECK_LAUNCH();
+      update_kernel<<<dim3(nblk, 1), kThreads, smh, st>>>(Vd, d, 0, n, hp, n, wd, 0, d,
+                                                          pass == 1 ? npart : nullptr);
+      count_launch();
+      FQ_CHECK_LAUNCH();
+    }
+    add_kernel_launch(h1, h2, n, 1, hd, 0, st);
+    FQ_CHECK_LAUNCH();
+  } else {
+    update_kernel<<<dim3(nblk, 1), kThreads, 0, st>>>(Vd, d, 0, 0, nullptr, 0, wd, 0, d, npart);
+    count_launch();
+    FQ_CHECK_LAUNCH();
+  }
+  norm_finalize_kernel<<<1, kThreads, 0, st>>>(npart, nblk, hd, 0, n, beta);
+  count_launch();
+  FQ_CHECK_LAUNCH();
+  const unsigned gx = (unsigned)std::min<int64_t>((d + kThreads - 1) / kThreads, 4096);
+  scale_kernel<<<dim3(gx, 1), kThreads, 0, st>>>(wd, 0, beta, wd, 0, d);
+  count_launch();
+  FQ_CHECK_LAUNCH();
+  set_error("%s", "");
+  return FLOQUET_OK;
+}

@@ -35,6 +35,8 @@ SIGNATURES = {
     "filter_apply": (_c_int, [_c_void_p, _c_double, _c_int64, _c_void_p, _c_void_p, _c_int,
                               _c_int, _c_int, _c_void_p]),
     "gram_schmidt": (_c_int, [_c_int64, _c_void_p, _c_int, _c_void_p, _dptr, _c_void_p]),
+    "gram_schmidt_noalloc": (_c_int, [_c_int64, _c_void_p, _c_int, _c_void_p, _c_void_p,
+                                      _c_void_p]),
     "small_eig": (_c_int, [_c_int, _c_void_p, _dptr, _c_void_p, _c_void_p]),
     "ritz_residuals": (_c_int, [_c_void_p, _c_void_p, _c_int, _dptr, _dptr, _c_void_p]),
     "arnoldi_eigs": (_c_int, [_c_void_p, _c_double, _c_int64, _c_int, _c_int, _c_int, _c_double,
@@ -203,6 +205,14 @@ def gram_schmidt(V, n, w, stream=None):
     h = np.zeros(2 * (n + 1))
     _check(lib().gram_schmidt(d, _ptr(V), n, _ptr(w), _dp(h), _stream(stream)), "gram_schmidt")
     return h[0::2] + 1j * h[1::2]
+
+
+def gram_schmidt_noalloc(V, n, w, h, stream=None):
+    """gram_schmidt with no device allocation: h is a caller-owned device tensor of n+1
+    complex128 (coefficients, then beta); asynchronous on the stream."""
+    _check(lib().gram_schmidt_noalloc(w.numel(), _ptr(V), n, _ptr(w), _ptr(h), _stream(stream)),
+           "gram_schmidt_noalloc")
+    return h
 
 
 def small_eig(A, Y=None, stream=None):
