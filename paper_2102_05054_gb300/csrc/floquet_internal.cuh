@@ -169,9 +169,19 @@ template <typename Real> struct PassArgs {
   const cplx<Real>* psi_in;
 };
 
-// Launch one pass for `nvec` vectors. `swap` selects the cot form of the butterfly.
+// Launch shapes of the pass kernel that the autotuner chooses from, per sweep precision: the
+// tile of 2^NB amplitudes (the plan's pass structure follows from it) and 2^RB amplitudes
+// per thread.
+struct PassVariant {
+  int NB, RB;
+};
+template <typename Real> int num_variants();
+template <typename Real> PassVariant variant_info(int v);
+// Launch one pass for `nvec` vectors with launch shape `v` (tiles smaller than the variant's
+// use the generic kernel). `swap` selects the cot form of the butterfly.
 template <typename Real>
-int launch_pass(const PassArgs<Real>& a, int epi, bool swap, int nvec, cudaStream_t st);
+int launch_pass_variant(int v, const PassArgs<Real>& a, int epi, bool swap, int nvec,
+                        cudaStream_t st);
 
 // Elementwise helpers (uapply.cu)
 template <typename Rin, typename Rout>
@@ -221,7 +231,11 @@ struct floquet_op {
   double tau;             // butterfly multiplier
   bool swap;              // cot form
   fq::BatchTables tabs;
-  fq::Plan plan64, plan32;
+  // per sweep precision, indexed by floquet_dtype (C128, C64, C128_DF): chosen launch shape,
+  // its pass plan, and whether the autotuner has run
+  fq::Plan plan[3];
+  int variant[3] = {0, 0, 0};
+  bool tuned[3] = {false, false, false};
   // filter workspace (lazily sized)
   void* work = nullptr;
   void* acc = nullptr;

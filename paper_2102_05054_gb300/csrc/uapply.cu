@@ -26,6 +26,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -133,294 +134,8 @@ void reset_launch_count() {
   g_launches = 0;
 }
 
-// ------------------------------------------------------------------ double-float arithmetic
-
-// Error-free transformations on the FP32 pipes (Dekker / Knuth two-sum and an FMA-based
-// two-product). The _rn intrinsics keep the compiler from contracting or reassociating.
-__device__ __forceinline__ float2 df_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return make_float2(s, e);
-}
-__device__ __forceinline__ float2 df_quick_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-// x + t * y for double-float x, t, y
-__device__ __forceinline__ float2 df_fma(float2 t, float2 y, float2 x) {
-  const float p = __fmul_rn(t.x, y.x);
-  const float pe = __fmaf_rn(t.x, y.x, -p);
-  const float2 s = df_two_sum(x.x, p);
-  const float lo = __fadd_rn(__fadd_rn(s.y, pe), __fmaf_rn(t.x, y.y, __fmaf_rn(t.y, y.x, x.y)));
-  return df_quick_two_sum(s.x, lo);
-}
-__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  const float e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -p)));
-  return df_quick_two_sum(p, e);
-}
-
-// ------------------------------------------------------------------ per-precision arithmetic
-
-// Butterfly x' = x - i tau y, y' = y - i tau x (one rounding per real output).
-__device__ __forceinline__ void bfly(float2 x, float2 y, float tau, float2& xn, float2& yn) {
-  xn = make_float2(fmaf(tau, y.y, x.x), fmaf(-tau, y.x, x.y));
-  yn = make_float2(fmaf(tau, x.y, y.x), fmaf(-tau, x.x, y.y));
-}
-__device__ __forceinline__ void bfly(double2 x, double2 y, double tau, double2& xn,
-                                     double2& yn) {
-  xn = make_double2(fma(tau, y.y, x.x), fma(-tau, y.x, x.y));
-  yn = make_double2(fma(tau, x.y, y.x), fma(-tau, x.x, y.y));
-}
-__device__ __forceinline__ void bfly(float4 x, float4 y, float2 tau, float4& xn, float4& yn) {
-  // re(x') = re x + tau im y, im(x') = im x - tau re y
-  const float2 nt = df_neg(tau);
-  const float2 a = df_fma(tau, make_float2(y.z, y.w), make_float2(x.x, x.y));
-  const float2 b = df_fma(nt, make_float2(y.x, y.y), make_float2(x.z, x.w));
-  const float2 c = df_fma(tau, make_float2(x.z, x.w), make_float2(y.x, y.y));
-  const float2 d = df_fma(nt, make_float2(x.x, x.y), make_float2(y.z, y.w));
-  xn = make_float4(a.x, a.y, b.x, b.y);
-  yn = make_float4(c.x, c.y, d.x, d.y);
-}
-
-// a * b (complex)
-__device__ __forceinline__ float2 zmul(float2 a, float2 b) { return cmul(a, b); }
-__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return cmul(a, b); }
-__device__ __forceinline__ float4 zmul(float4 a, float4 b) {
-  const float2 ar = make_float2(a.x, a.y), ai = make_float2(a.z, a.w);
-  const float2 br = make_float2(b.x, b.y), bi = make_float2(b.z, b.w);
-  const float2 re = df_fma(ar, br, df_mul(df_neg(ai), bi));
-  const float2 im = df_fma(ar, bi, df_mul(ai, br));
-  return make_float4(re.x, re.y, im.x, im.y);
-}
-// acc + c * v (complex)
-__device__ __forceinline__ float2 zfma(float2 c, float2 v, float2 acc) { return cfma(c, v, acc); }
-__device__ __forceinline__ double2 zfma(double2 c, double2 v, double2 acc) {
-  return cfma(c, v, acc);
-}
-__device__ __forceinline__ float4 zfma(float4 c, float4 v, float4 acc) {
-  const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
-  const float2 vr = make_float2(v.x, v.y), vi = make_float2(v.z, v.w);
-  const float2 re = df_fma(cr, vr, df_fma(df_neg(ci), vi, make_float2(acc.x, acc.y)));
-  const float2 im = df_fma(cr, vi, df_fma(ci, vr, make_float2(acc.z, acc.w)));
-  return make_float4(re.x, re.y, im.x, im.y);
-}
-
-// ------------------------------------------------------------------ pass kernel
-
-// Tile element e -> position in padded shared memory (one pad slot every 2^RB elements
-// keeps the strided transposes free of bank conflicts).
-template <int RB> __device__ __forceinline__ int smem_pos(int e) { return e + (e >> RB); }
-
-// Element index of register r of thread t when the register bits are tile bits [g, g+RB).
-template <int RB> __device__ __forceinline__ int tile_elem(int t, int r, int g) {
-  return (t & ((1 << g) - 1)) | (r << g) | ((t >> g) << (g + RB));
-}
-
-template <typename Real, int RB, bool SWAP>
-__device__ __forceinline__ void kick_registers(cplx<Real> (&v)[1 << RB], int g, int lo, int hi,
-                                               scal<Real> tau) {
-#pragma unroll
-  for (int b = 0; b < RB; ++b) {
-    const int bit = g + b;
-    if (bit >= lo && bit < hi) {
-#pragma unroll
-      for (int r = 0; r < (1 << RB); ++r) {
-        if (r & (1 << b)) continue;
-        cplx<Real> xn, yn;
-        bfly(v[r], v[r | (1 << b)], tau, xn, yn);
-        if (SWAP) {
-          v[r] = yn;
-          v[r | (1 << b)] = xn;
-        } else {
-          v[r] = xn;
-          v[r | (1 << b)] = yn;
-        }
-      }
-    }
-  }
-}
-
-// NBT > 0: the tile size 2^NBT is a compile-time constant (the large tiles of the hot path),
-// so every shared-memory index folds to a per-thread base plus a constant; NBT == 0: the
-// tile size A.NB is read at run time (small states).
-template <typename Real, int NBT, int RB, int EPI, bool SWAP>
-__global__ void __launch_bounds__(256) pass_kernel(const PassArgs<Real> A) {
-  using C = cplx<Real>;
-  constexpr int R = 1 << RB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-
-  const int NB = NBT > 0 ? NBT : A.NB;
-  const int t = threadIdx.x;
-  // flattened grid: blockIdx.x = vec * ntiles + tile (ntiles = 2^(L - NB))
-  const int tilebits = A.L - NB;
-  const int64_t vec = (int64_t)(blockIdx.x >> tilebits);
-  const uint32_t cta = blockIdx.x & ((1u << tilebits) - 1u);
-  const uint32_t mid = cta & ((1u << A.midbits) - 1u);
-  const uint32_t top = cta >> A.midbits;
-  const int c = A.c, start = A.start;
-  const uint32_t cmask = (1u << c) - 1u;
-  // global index of element e = t | (r << g_top): tbase + roff[r] (t and r bits are disjoint)
-  const int g_top = NB - RB;
-  const uint32_t tb = (uint32_t)t;
-  const uint32_t tbase = ((mid << c) | (top << A.topshift)) + (tb & cmask) + ((tb >> c) << start);
-  uint32_t roff[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const uint32_t er = (uint32_t)r << g_top;
-    roff[r] = (er & cmask) + ((er >> c) << start);
-  }
-
-  // Programmatic dependent launch: let the next pass be scheduled now (it waits for this
-  // grid's completion before touching memory), then wait for the previous pass.
-  asm volatile("griddepcontrol.launch_dependents;");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-
-  const C* __restrict__ src = A.src + vec * A.d;
-  C v[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = src[tbase + roff[r]];
-  // For complex64 (latency bound) the epilogue's other operand, the accumulator or Horner's
-  // psi_in, is loaded together with the state so that its latency overlaps the kicks; the
-  // wider types are arithmetic bound and keep their registers for the sweep instead.
-  constexpr bool kPrefetch =
-      (EPI == EPI_PHASE_ACC || EPI == EPI_PHASE_HORNER) && sizeof(C) == 8;
-  const C* __restrict__ other = (EPI == EPI_PHASE_ACC ? A.acc : A.psi_in) + vec * A.d;
-  C pre[kPrefetch ? R : 1];
-  if (kPrefetch) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) pre[r] = other[tbase + roff[r]];
-  }
-
-  // Round 0: register bits are the top RB tile bits.
-  int hi = NB;
-  int g = g_top;
-  kick_registers<Real, RB, SWAP>(v, g, A.kick_from, hi, A.tau);
-  hi = g;
-  bool first_transpose = true;
-  while (hi > A.kick_from) {
-    const int gn = (hi - RB) > 0 ? (hi - RB) : 0;
-    if (!first_transpose) __syncthreads();
-    first_transpose = false;
-#pragma unroll
-    for (int r = 0; r < R; ++r) sm[smem_pos<RB>(tile_elem<RB>(t, r, g))] = v[r];
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sm[smem_pos<RB>(tile_elem<RB>(t, r, gn))];
-    g = gn;
-    kick_registers<Real, RB, SWAP>(v, g, A.kick_from, hi, A.tau);
-    hi = g;
-  }
-  if (g != g_top) {  // back to the coalesced mapping
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < R; ++r) sm[smem_pos<RB>(tile_elem<RB>(t, r, g))] = v[r];
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sm[smem_pos<RB>(tile_elem<RB>(t, r, g_top))];
-  }
-
-  C* __restrict__ dst = A.dst + vec * A.d;
-  if (EPI == EPI_STORE) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) dst[tbase + roff[r]] = v[r];
-    return;
-  }
-  const int64_t prob = vec / A.vec_per_prob;
-  const C* __restrict__ tlo = A.tab_lo + prob * A.tab_lo_stride;
-  const C* __restrict__ thi = A.tab_hi + prob * A.tab_hi_stride;
-  const uint32_t lomask = (1u << A.a) - 1u;
-  const int am1 = A.a - 1;
-  C cj;
-  if (EPI == EPI_PHASE_ACC) cj = A.coef[vec * A.coef_stride + A.jstep];
-  if (EPI == EPI_PHASE_HORNER) cj = A.coef[vec * A.coef_stride];
-  C* __restrict__ acc = A.acc + vec * A.d;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const uint32_t s = tbase + roff[r];
-    const C p = zmul(__ldg(&tlo[s & lomask]), __ldg(&thi[((s >> am1) << 1) | (s & 1u)]));
-    const C val = zmul(p, v[r]);
-    if (EPI == EPI_PHASE) {
-      dst[s] = val;
-    } else {
-      const C o = kPrefetch ? pre[kPrefetch ? r : 0] : other[s];
-      if (EPI == EPI_PHASE_ACC) {
-        dst[s] = val;
-        acc[s] = zfma(cj, val, o);
-      } else {  // Horner: dst (= acc) = psi_in + z * U acc
-        dst[s] = zfma(cj, val, o);
-      }
-    }
-  }
-}
-
-template <typename Real, int NBT, int RB, int EPI, bool SWAP>
-static int launch_pass_t(const PassArgs<Real>& a, int nvec, cudaStream_t st) {
-  const int threads = 1 << (a.NB - RB);
-  // at most (2^12 + 2^8) * 8 or (2^11 + 2^8) * 16 bytes: below the 48 KiB default
-  const size_t smem = (size_t)((1 << a.NB) + (1 << (a.NB - RB))) * sizeof(cplx<Real>);
-  const int64_t ntiles = (int64_t)1 << (a.L - a.NB);
-  if (ntiles * nvec > 0x7fffffffLL) {
-    set_error("launch_pass: grid too large (nvec %d, tiles %lld)", nvec, (long long)ntiles);
-    return FLOQUET_EINVAL;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(ntiles * nvec));
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  FQ_CUDA(cudaLaunchKernelEx(&cfg, pass_kernel<Real, NBT, RB, EPI, SWAP>, a));
-  count_launch();
-  FQ_CHECK_LAUNCH();
-  return FLOQUET_OK;
-}
-
-template <typename Real, int NBT, int RB>
-static int dispatch_epi(const PassArgs<Real>& a, int epi, bool swap, int nvec, cudaStream_t st) {
-  switch (epi * 2 + (swap ? 1 : 0)) {
-    case 0: return launch_pass_t<Real, NBT, RB, EPI_STORE, false>(a, nvec, st);
-    case 1: return launch_pass_t<Real, NBT, RB, EPI_STORE, true>(a, nvec, st);
-    case 2: return launch_pass_t<Real, NBT, RB, EPI_PHASE, false>(a, nvec, st);
-    case 3: return launch_pass_t<Real, NBT, RB, EPI_PHASE, true>(a, nvec, st);
-    case 4: return launch_pass_t<Real, NBT, RB, EPI_PHASE_ACC, false>(a, nvec, st);
-    case 5: return launch_pass_t<Real, NBT, RB, EPI_PHASE_ACC, true>(a, nvec, st);
-    case 6: return launch_pass_t<Real, NBT, RB, EPI_PHASE_HORNER, false>(a, nvec, st);
-    case 7: return launch_pass_t<Real, NBT, RB, EPI_PHASE_HORNER, true>(a, nvec, st);
-  }
-  set_error("launch_pass: bad epilogue %d", epi);
-  return FLOQUET_EINVAL;
-}
-
-// Largest tile (bits) per precision: 2^12 complex64 (34 KiB of shared memory with padding),
-// 2^11 complex128 or double-float (36 KiB).
-template <typename Real> static constexpr int max_tile_bits() { return 11; }
-template <> constexpr int max_tile_bits<float>() { return 12; }
-
-// Register bits per thread: 16 complex64 or 8 complex128 / double-float complex (32
-// registers of data either way); a tile smaller than 2^4 complex64 uses 3.
-template <typename Real>
-int launch_pass(const PassArgs<Real>& a, int epi, bool swap, int nvec, cudaStream_t st) {
-  constexpr int NBM = max_tile_bits<Real>();
-  if constexpr (std::is_same<Real, float>::value) {
-    if (a.NB == NBM) return dispatch_epi<Real, NBM, 4>(a, epi, swap, nvec, st);
-    if (a.NB >= 4) return dispatch_epi<Real, 0, 4>(a, epi, swap, nvec, st);
-    return dispatch_epi<Real, 0, 3>(a, epi, swap, nvec, st);
-  } else {
-    if (a.NB == NBM) return dispatch_epi<Real, NBM, 3>(a, epi, swap, nvec, st);
-    return dispatch_epi<Real, 0, 3>(a, epi, swap, nvec, st);
-  }
-}
-template int launch_pass<float>(const PassArgs<float>&, int, bool, int, cudaStream_t);
-template int launch_pass<double>(const PassArgs<double>&, int, bool, int, cudaStream_t);
-template int launch_pass<dfloat>(const PassArgs<dfloat>&, int, bool, int, cudaStream_t);
+// The pass kernel itself is in pass_kernel.cuh, instantiated per sweep precision in
+// pass_f32.cu, pass_f64.cu and pass_df.cu.
 
 // ------------------------------------------------------------------ elementwise kernels
 
@@ -519,6 +234,11 @@ static int launch_convert_strided(const cplx<Rin>* in, cplx<Rout>* out, int64_t 
 // ------------------------------------------------------------------ operator set-up
 
 
+template <typename Real> static int sweep_dtype();
+template <> int sweep_dtype<float>() { return FLOQUET_C64; }
+template <> int sweep_dtype<double>() { return FLOQUET_C128; }
+template <> int sweep_dtype<dfloat>() { return FLOQUET_C128_DF; }
+
 // Split the L qubits into passes: the first kicks the NB lowest qubits in contiguous tiles;
 // each later pass keeps at least `min_cols` low (contiguous) bits in its tile for coalescing
 // and kicks up to NB - min_cols further qubits.
@@ -564,6 +284,16 @@ static PassArgs<Real> make_args(const floquet_op* op, const Pass& ps, const cplx
   a.tab_hi_stride = op->tabs.hi_n;
   a.vec_per_prob = 1;
   return a;
+}
+
+// Column bits kept in the later passes' tiles: 4 complex64 (32-byte row segments) or 3
+// wider elements (48-byte segments).
+template <typename Real> static int min_cols() { return sizeof(cplx<Real>) == 8 ? 4 : 3; }
+
+template <typename Real> static void set_variant(floquet_op* op, int v) {
+  const int t = sweep_dtype<Real>();
+  op->variant[t] = v;
+  op->plan[t] = make_plan(op->L, variant_info<Real>(v).NB, min_cols<Real>());
 }
 
 int op_init(floquet_op* op, int L, double J, double g, const double* h, int nprob) {
@@ -642,8 +372,9 @@ int op_init(floquet_op* op, int L, double J, double g, const double* h, int npro
   FQ_CUDA(cudaMemcpy(T.hi64, hi.data(), hi.size() * sizeof(double2), cudaMemcpyHostToDevice));
   FQ_CUDA(cudaMemcpy(T.lo32, lo32.data(), lo.size() * sizeof(float2), cudaMemcpyHostToDevice));
   FQ_CUDA(cudaMemcpy(T.hi32, hi32.data(), hi.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  op->plan32 = make_plan(L, max_tile_bits<float>(), 4);
-  op->plan64 = make_plan(L, max_tile_bits<double>(), 3);
+  set_variant<float>(op, 0);
+  set_variant<double>(op, 0);
+  set_variant<dfloat>(op, 0);
   return FLOQUET_OK;
 }
 
@@ -669,15 +400,10 @@ void op_free(floquet_op* op) {
   cudaFree(op->coef);
 }
 
-template <typename Real> static int sweep_dtype();
-template <> int sweep_dtype<float>() { return FLOQUET_C64; }
-template <> int sweep_dtype<double>() { return FLOQUET_C128; }
-template <> int sweep_dtype<dfloat>() { return FLOQUET_C128_DF; }
-
 template <typename Real> static const Plan& plan_of(const floquet_op* op);
-template <> const Plan& plan_of<float>(const floquet_op* op) { return op->plan32; }
-template <> const Plan& plan_of<double>(const floquet_op* op) { return op->plan64; }
-template <> const Plan& plan_of<dfloat>(const floquet_op* op) { return op->plan64; }
+template <typename Real> const Plan& plan_of(const floquet_op* op) {
+  return op->plan[sweep_dtype<Real>()];
+}
 template <typename Real> static const cplx<Real>* tlo_of(const floquet_op* op);
 template <> const float2* tlo_of<float>(const floquet_op* op) { return op->tabs.lo32; }
 template <> const double2* tlo_of<double>(const floquet_op* op) { return op->tabs.lo64; }
@@ -708,14 +434,78 @@ static int u_passes(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int n
       a.jstep = jstep;
       a.psi_in = psi_in;
     }
-    FQ_TRY(launch_pass<Real>(a, last ? epi : EPI_STORE, op->swap, nvec, st));
+    FQ_TRY(launch_pass_variant<Real>(op->variant[sweep_dtype<Real>()], a,
+                                     last ? epi : EPI_STORE, op->swap, nvec, st));
   }
   return FLOQUET_OK;
+}
+
+static void destroy_graphs(floquet_op* op);
+
+// Autotuner: the first U application in a sweep precision on an operator with L >= 14 times
+// every launch shape of that precision (3 warm-up and 10 timed applications of U to one
+// scratch state, CUDA events on the caller's stream) and keeps the fastest; smaller states
+// keep the first shape. It runs before any filter graph of the operator is captured, and
+// drops the operator's cached graphs when it changes the plan.
+template <typename Real> static int tune(floquet_op* op, int nvec, cudaStream_t st) {
+  const int t = sweep_dtype<Real>();
+  if (op->tuned[t]) return FLOQUET_OK;
+  op->tuned[t] = true;
+  const int nv = num_variants<Real>();
+  if (const char* forced = getenv("FLOQUET_PASS_VARIANT")) {  // fixed shape, e.g. to profile
+    const int v = atoi(forced);
+    if (v >= 0 && v < nv && variant_info<Real>(v).NB <= op->L) {
+      set_variant<Real>(op, v);
+      destroy_graphs(op);
+    }
+    return FLOQUET_OK;
+  }
+  if (op->L < 13 || nv < 2) return FLOQUET_OK;
+  // time with the caller's batch width (capped), since the best tile depends on how many
+  // CTAs the whole launch has
+  const int nt = std::max(1, std::min(nvec, std::max(1, (int)((int64_t(64) << 20) / op->d))));
+  cplx<Real>* buf = nullptr;
+  FQ_CUDA(cudaMalloc(&buf, sizeof(cplx<Real>) * op->d * nt));
+  FQ_CUDA(cudaMemsetAsync(buf, 0, sizeof(cplx<Real>) * op->d * nt, st));
+  cudaEvent_t e0, e1;
+  FQ_CUDA(cudaEventCreate(&e0));
+  FQ_CUDA(cudaEventCreate(&e1));
+  float best = 3.0e38f;
+  int bestv = 0;
+  int rc = FLOQUET_OK;
+  for (int v = 0; v < nv && rc == FLOQUET_OK; ++v) {
+    set_variant<Real>(op, v);
+    if (variant_info<Real>(v).NB > op->L) continue;
+    for (int i = 0; i < 3 && rc == FLOQUET_OK; ++i)
+      rc = u_passes<Real>(op, buf, buf, nt, nt, EPI_PHASE, nullptr, nullptr, 0, 0, nullptr, st);
+    cudaEventRecord(e0, st);
+    for (int i = 0; i < 10 && rc == FLOQUET_OK; ++i)
+      rc = u_passes<Real>(op, buf, buf, nt, nt, EPI_PHASE, nullptr, nullptr, 0, 0, nullptr, st);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = FLOQUET_ECUDA;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (getenv("FLOQUET_VERBOSE"))
+      fprintf(stderr, "floquet tune: L=%d dtype=%d nvec=%d shape (NB=%d, RB=%d): %.2f us per U\n",
+              op->L, t, nt, variant_info<Real>(v).NB, variant_info<Real>(v).RB, 1000.0 * ms / 10);
+    if (rc == FLOQUET_OK && ms < best) {
+      best = ms;
+      bestv = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(buf);
+  set_variant<Real>(op, bestv);
+  destroy_graphs(op);
+  return rc;
 }
 
 template <typename Real>
 int apply_u(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int nvec, int vec_per_prob,
             cudaStream_t st) {
+  FQ_TRY(tune<Real>(op, nvec, st));
   return u_passes<Real>(op, in, out, nvec, vec_per_prob, EPI_PHASE, nullptr, nullptr, 0, 0,
                         nullptr, st);
 }
@@ -827,6 +617,7 @@ int filter_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio
                 int vec_per_prob, bool use_graph, cudaStream_t st) {
   using C = cplx<Real>;
   const int64_t d = op->d;
+  FQ_TRY(tune<Real>(op, nvec, st));
   FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
   C* work = reinterpret_cast<C*>(op->work);
   C* acc = reinterpret_cast<C*>(op->acc);
@@ -850,6 +641,7 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
                   int vec_per_prob, bool use_graph, cudaStream_t st) {
   using C = cplx<Real>;
   const int64_t d = op->d;
+  FQ_TRY(tune<Real>(op, nvec, st));
   FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
   C* pin = reinterpret_cast<C*>(op->psi_in_copy);
   C* acc = reinterpret_cast<C*>(op->acc);
