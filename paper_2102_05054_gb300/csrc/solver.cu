@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -530,24 +532,40 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
       FQ_CUDA(cudaMemcpyAsync(X0, Xn.p, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
       break;
     }
-    // R = U x - omega x; corr = q(U) R in complex64 sweeps; Y = g(omega) x + corr
+    // R = U x - omega x; corr = q(U) R in complex64 sweeps; Y = g(omega) x + corr. Pairs
+    // already ten times below the residual target are locked: they stay in the Rayleigh-Ritz
+    // space as they are and are not filtered again.
     FQ_TRY(residual_vectors(Xn.p, corr.p, R.p, d, nb, rq.p, st));
-    for (int i = 0; i < nb; ++i) {
+    std::vector<int> act;
+    for (int i = 0; i < nb; ++i)
+      if (rq_h[3 * i + 2] > 0.1 * tol_resid) act.push_back(i);
+    const int nf = (int)act.size();
+    if (getenv("FLOQUET_VERBOSE"))
+      fprintf(stderr, "floquet polish: iter %d block %d worst selected resid %.3e, filtering %d\n",
+              it, nb, worst, nf);
+    for (int j = 0; j < nf; ++j) {
+      const int i = act[j];
+      if (i != j)
+        FQ_CUDA(cudaMemcpyAsync(R.p + (size_t)j * d, R.p + (size_t)i * d, sizeof(double2) * d,
+                                cudaMemcpyDeviceToDevice, st));
       cd gv;
-      defect_coefficients(om[i], phi, k, coef_h.data() + (size_t)i * (k - 1), &gv);
-      g_h[i] = make_double2(gv.real(), gv.imag());
+      defect_coefficients(om[i], phi, k, coef_h.data() + (size_t)j * (k - 1), &gv);
+      g_h[j] = make_double2(gv.real(), gv.imag());
     }
-    FQ_CUDA(cudaMemcpyAsync(coef.p, coef_h.data(), sizeof(float2) * coef_h.size(),
+    FQ_CUDA(cudaMemcpyAsync(coef.p, coef_h.data(), sizeof(float2) * (size_t)nf * (k - 1),
                             cudaMemcpyHostToDevice, st));
-    FQ_CUDA(cudaMemcpyAsync(gvals.p, g_h.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice,
+    FQ_CUDA(cudaMemcpyAsync(gvals.p, g_h.data(), sizeof(double2) * nf, cudaMemcpyHostToDevice,
                             st));
-    FQ_TRY((filter_coef<float, double>(op, R.p, d, corr.p, d, coef.p, k - 1, nb, nb, true, st)));
-    FQ_TRY(axpy_cols(Xn.p, corr.p, d, nb, gvals.p, st));
-    // S = orth([Xn, Y])
+    FQ_TRY((filter_coef<float, double>(op, R.p, d, corr.p, d, coef.p, k - 1, nf, nf, true, st)));
+    // S = orth([Xn, Y_active]) with Y_j = g(omega_j) x_j + corr_j
     FQ_CUDA(cudaMemcpyAsync(S.p, Xn.p, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
-    FQ_CUDA(cudaMemcpyAsync(S.p + (size_t)nb * d, corr.p, sizeof(double2) * nb * d,
+    for (int j = 0; j < nf; ++j)
+      FQ_CUDA(cudaMemcpyAsync(R.p + (size_t)j * d, Xn.p + (size_t)act[j] * d,
+                              sizeof(double2) * d, cudaMemcpyDeviceToDevice, st));
+    FQ_TRY(axpy_cols(R.p, corr.p, d, nf, gvals.p, st));
+    FQ_CUDA(cudaMemcpyAsync(S.p + (size_t)nb * d, corr.p, sizeof(double2) * nf * d,
                             cudaMemcpyDeviceToDevice, st));
-    ns = n2;
+    ns = nb + nf;
     FQ_TRY(orthonormalize(ws, S.p, ns, d, st));
   }
   return FLOQUET_OK;
