@@ -459,7 +459,7 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
            std::vector<double>& resid_out, std::vector<int>& cols_out, int* iters,
            cudaStream_t st) {
   const int n2 = 2 * nb;
-  DevBuf<double2> S, WS, Xn, G, Yg, lam, eigw, R, corr, gvals;
+  DevBuf<double2> S, WS, Xn, G, Yg, lam, eigw, R, corr;
   DevBuf<float2> coef;
   DevBuf<double> rq;
   DevBuf<int> info;
@@ -473,7 +473,6 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
   FQ_TRY(info.alloc(1));
   FQ_TRY(R.alloc((size_t)nb * d));
   FQ_TRY(corr.alloc((size_t)nb * d));
-  FQ_TRY(gvals.alloc(nb));
   FQ_TRY(rq.alloc((size_t)3 * n2));
   FQ_TRY(coef.alloc((size_t)nb * (k - 1)));
   // S[:, :nb] = X0 (orthonormalised)
@@ -482,7 +481,6 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
   int ns = nb;  // columns of S in use
   std::vector<double> rq_h(3 * n2);
   std::vector<float2> coef_h((size_t)nb * (k - 1));
-  std::vector<double2> g_h(nb);
   std::vector<double2> lam_h(n2);
   for (int it = 0;; ++it) {
     // Rayleigh-Ritz with U on span(S): G = S^H U S, G = Yg diag Yg^{-1}
@@ -550,19 +548,15 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
                                 cudaMemcpyDeviceToDevice, st));
       cd gv;
       defect_coefficients(om[i], phi, k, coef_h.data() + (size_t)j * (k - 1), &gv);
-      g_h[j] = make_double2(gv.real(), gv.imag());
     }
     FQ_CUDA(cudaMemcpyAsync(coef.p, coef_h.data(), sizeof(float2) * (size_t)nf * (k - 1),
                             cudaMemcpyHostToDevice, st));
-    FQ_CUDA(cudaMemcpyAsync(gvals.p, g_h.data(), sizeof(double2) * nf, cudaMemcpyHostToDevice,
-                            st));
     FQ_TRY((filter_coef<float, double>(op, R.p, d, corr.p, d, coef.p, k - 1, nf, nf, true, st)));
-    // S = orth([Xn, Y_active]) with Y_j = g(omega_j) x_j + corr_j
+    // span(S) = span(Xn, g_k(U) Xn_active) = span(Xn, corr_active): the filtered vector is
+    // g(omega) x + corr and its x part is already in span(Xn). Appending corr rather than the
+    // filtered vector avoids the cancellation (||corr|| ~ 1e-9 ||g x|| once converged) that
+    // would leave the orthonormalised basis non-orthogonal at the 1e-6 level.
     FQ_CUDA(cudaMemcpyAsync(S.p, Xn.p, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
-    for (int j = 0; j < nf; ++j)
-      FQ_CUDA(cudaMemcpyAsync(R.p + (size_t)j * d, Xn.p + (size_t)act[j] * d,
-                              sizeof(double2) * d, cudaMemcpyDeviceToDevice, st));
-    FQ_TRY(axpy_cols(R.p, corr.p, d, nf, gvals.p, st));
     FQ_CUDA(cudaMemcpyAsync(S.p + (size_t)nb * d, corr.p, sizeof(double2) * nf * d,
                             cudaMemcpyDeviceToDevice, st));
     ns = nb + nf;
