@@ -447,18 +447,50 @@ static void defect_coefficients(cd omega, double phi, int64_t k, float2* out,
   }
 }
 
-static int orthonormalize(Workspace& ws, double2* X, int n, int64_t d, cudaStream_t st) {
-  for (int j = 0; j < n; ++j)
-    FQ_TRY(cgs2(ws, X, d, 0, j, X + (int64_t)j * d, 0, d, 1, nullptr, 0, X + (int64_t)j * d, 0,
-                st));
+// Orthonormalise the columns of X in place, one at a time: each column is normalised, then
+// projected twice against the columns kept so far (CGS2); a column whose new component is
+// below `drop` of its length adds no direction and is dropped (later columns move up).
+// Without the drop, nearly dependent columns would leave the basis non-orthogonal at the
+// drop level / eps ratio and the Rayleigh-Ritz step would mix eigenvectors.
+static int orthonormalize(Workspace& ws, double2* X, int n, int64_t d, double drop, int* kept,
+                          cudaStream_t st) {
+  int w = 0;
+  double beta = 0;
+  for (int j = 0; j < n; ++j) {
+    double2* col = X + (int64_t)w * d;
+    if (j != w)
+      FQ_CUDA(cudaMemcpyAsync(col, X + (int64_t)j * d, sizeof(double2) * d,
+                              cudaMemcpyDeviceToDevice, st));
+    // normalise (no projection), then project against the kept columns
+    FQ_TRY(cgs2(ws, X, d, 0, 0, col, 0, d, 1, nullptr, 0, col, 0, st));
+    FQ_CUDA(cudaMemcpyAsync(&beta, ws.last_betas, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FQ_CUDA(cudaStreamSynchronize(st));
+    if (!(beta > 0)) continue;
+    if (w > 0) {
+      FQ_TRY(cgs2(ws, X, d, 0, w, col, 0, d, 1, nullptr, 0, col, 0, st));
+      FQ_CUDA(cudaMemcpyAsync(&beta, ws.last_betas, sizeof(double), cudaMemcpyDeviceToHost, st));
+      FQ_CUDA(cudaStreamSynchronize(st));
+      if (!(beta > drop)) continue;
+    }
+    ++w;
+  }
+  *kept = w;
   return FLOQUET_OK;
 }
 
+// FP64 polish of the FILTER_FP32 result (Sec. 4 footnote: a Ritz step with U on approximate
+// eigenvectors, here iterated). Each iteration: Rayleigh-Ritz with U on span(S); keep the nb
+// Ritz pairs with the largest |g_k(omega)| (the block the filter enhances); stop when the nev
+// closest in-lobe pairs have residuals <= tol_resid; otherwise extend S by the
+// defect-corrected filter directions q(U) r of the unconverged pairs, where
+// g_k(U) x = g_k(omega) x + q(U) r and r = (U - omega) x is computed in FP64, so the
+// complex64 sweeps only act on the small residual.
 int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double tol_resid,
            int max_iter, double2* X0, int nb, int64_t d, std::vector<cd>& omega_out,
            std::vector<double>& resid_out, std::vector<int>& cols_out, int* iters,
            cudaStream_t st) {
   const int n2 = 2 * nb;
+  const bool verbose = getenv("FLOQUET_VERBOSE") != nullptr;
   DevBuf<double2> S, WS, Xn, G, Yg, lam, eigw, R, corr;
   DevBuf<float2> coef;
   DevBuf<double> rq;
@@ -475,48 +507,55 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
   FQ_TRY(corr.alloc((size_t)nb * d));
   FQ_TRY(rq.alloc((size_t)3 * n2));
   FQ_TRY(coef.alloc((size_t)nb * (k - 1)));
-  // S[:, :nb] = X0 (orthonormalised)
+  const double drop = 1e-6;
   FQ_CUDA(cudaMemcpyAsync(S.p, X0, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
-  FQ_TRY(orthonormalize(ws, S.p, nb, d, st));
-  int ns = nb;  // columns of S in use
+  int ns = 0;
+  FQ_TRY(orthonormalize(ws, S.p, nb, d, drop, &ns, st));
   std::vector<double> rq_h(3 * n2);
   std::vector<float2> coef_h((size_t)nb * (k - 1));
   std::vector<double2> lam_h(n2);
+  int nk = 0;
   for (int it = 0;; ++it) {
-    // Rayleigh-Ritz with U on span(S): G = S^H U S, G = Yg diag Yg^{-1}
+    // Rayleigh-Ritz with U on span(S): G = S^H U S = Yg diag(lam) Yg^{-1}
     FQ_TRY(apply_u<double>(op, S.p, WS.p, ns, ns, st));
     FQ_TRY(gemm_cn(ws, S.p, d, 0, WS.p, d, 0, d, ns, ns, 1, G.p, ns, 0, st));
     FQ_TRY(small_eig_batched(G.p, ns, 0, ns, 1, lam.p, 0, Yg.p, ns, 0, eigw.p, info.p, st));
+    int info_h = 0;
     FQ_CUDA(cudaMemcpyAsync(lam_h.data(), lam.p, sizeof(double2) * ns, cudaMemcpyDeviceToHost,
                             st));
+    FQ_CUDA(cudaMemcpyAsync(&info_h, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     FQ_CUDA(cudaStreamSynchronize(st));
-    // keep the nb Ritz values with the largest |g_k(omega)| (the block the filter enhances)
+    if (info_h) {
+      set_error("polish: small eigensolver did not converge (n = %d)", ns);
+      return FLOQUET_ENOCONV;
+    }
+    // keep the nk = min(nb, ns) Ritz values with the largest |g_k(omega)|
+    nk = std::min(nb, ns);
     std::vector<int> order(ns);
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> gabs(ns);
     for (int i = 0; i < ns; ++i) gabs[i] = std::abs(gk_value(cd(lam_h[i].x, lam_h[i].y), phi, k));
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gabs[a] > gabs[b]; });
-    order.resize(nb);
-    // Xn = S Yg[:, order], Wn = WS Yg[:, order]  (via a permuted copy of Yg into G)
-    for (int i = 0; i < nb; ++i)
+    order.resize(nk);
+    for (int i = 0; i < nk; ++i)
       FQ_CUDA(cudaMemcpyAsync(G.p + (size_t)i * ns, Yg.p + (size_t)order[i] * ns,
                               sizeof(double2) * ns, cudaMemcpyDeviceToDevice, st));
-    FQ_TRY(gemm_nn(S.p, d, 0, G.p, ns, 0, Xn.p, d, 0, d, ns, nb, 1, st));
-    FQ_TRY(gemm_nn(WS.p, d, 0, G.p, ns, 0, corr.p, d, 0, d, ns, nb, 1, st));  // corr = U Xn
-    FQ_TRY(rayleigh_residual(ws, Xn.p, corr.p, d, nb, rq.p, st));
-    FQ_CUDA(cudaMemcpyAsync(rq_h.data(), rq.p, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost,
+    FQ_TRY(gemm_nn(S.p, d, 0, G.p, ns, 0, Xn.p, d, 0, d, ns, nk, 1, st));
+    FQ_TRY(gemm_nn(WS.p, d, 0, G.p, ns, 0, corr.p, d, 0, d, ns, nk, 1, st));  // U Xn
+    FQ_TRY(rayleigh_residual(ws, Xn.p, corr.p, d, nk, rq.p, st));
+    FQ_CUDA(cudaMemcpyAsync(rq_h.data(), rq.p, sizeof(double) * 3 * nk, cudaMemcpyDeviceToHost,
                             st));
     FQ_CUDA(cudaStreamSynchronize(st));
-    std::vector<cd> om(nb);
-    for (int i = 0; i < nb; ++i) om[i] = cd(rq_h[3 * i], rq_h[3 * i + 1]);
-    // Rayleigh-Ritz over [X, Y] also yields values inside the unit disk (mixtures of the
-    // correction directions); only values on the circle (eigenvalues of a unitary) inside
-    // the main lobe are candidates.
-    std::vector<cd> om_c(nb);
-    for (int i = 0; i < nb; ++i)
+    std::vector<cd> om(nk);
+    for (int i = 0; i < nk; ++i) om[i] = cd(rq_h[3 * i], rq_h[3 * i + 1]);
+    // Rayleigh-Ritz over an extended space also yields values inside the unit disk (mixtures
+    // of correction directions); only values on the circle inside the main lobe are
+    // candidates.
+    std::vector<cd> om_c(nk);
+    for (int i = 0; i < nk; ++i)
       om_c[i] = std::fabs(std::abs(om[i]) - 1.0) < 1e-4 ? om[i] : cd(0.0, 0.0);
     const std::vector<int> sel = select_closest(om_c, phi, k, nev, true);
-    double worst = 0;
+    double worst = sel.size() < (size_t)nev ? INFINITY : 0.0;
     for (int i : sel) worst = std::max(worst, rq_h[3 * i + 2]);
     omega_out.clear();
     resid_out.clear();
@@ -526,21 +565,20 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
       resid_out.push_back(rq_h[3 * i + 2]);
     }
     *iters = it;
-    if (worst <= tol_resid || it >= max_iter) {
-      FQ_CUDA(cudaMemcpyAsync(X0, Xn.p, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
-      break;
-    }
-    // R = U x - omega x; corr = q(U) R in complex64 sweeps; Y = g(omega) x + corr. Pairs
-    // already ten times below the residual target are locked: they stay in the Rayleigh-Ritz
-    // space as they are and are not filtered again.
-    FQ_TRY(residual_vectors(Xn.p, corr.p, R.p, d, nb, rq.p, st));
+    // residual vectors of the pairs still above a tenth of the target (the others are
+    // locked: they stay in the Rayleigh-Ritz space but are not filtered again)
     std::vector<int> act;
-    for (int i = 0; i < nb; ++i)
+    for (int i = 0; i < nk; ++i)
       if (rq_h[3 * i + 2] > 0.1 * tol_resid) act.push_back(i);
     const int nf = (int)act.size();
-    if (getenv("FLOQUET_VERBOSE"))
-      fprintf(stderr, "floquet polish: iter %d block %d worst selected resid %.3e, filtering %d\n",
-              it, nb, worst, nf);
+    if (verbose)
+      fprintf(stderr, "floquet polish: iter %d space %d block %d worst selected resid %.3e, "
+              "filtering %d\n", it, ns, nk, worst, nf);
+    if (worst <= tol_resid || it >= max_iter || nf == 0) {
+      FQ_CUDA(cudaMemcpyAsync(X0, Xn.p, sizeof(double2) * nk * d, cudaMemcpyDeviceToDevice, st));
+      break;
+    }
+    FQ_TRY(residual_vectors(Xn.p, corr.p, R.p, d, nk, rq.p, st));
     for (int j = 0; j < nf; ++j) {
       const int i = act[j];
       if (i != j)
@@ -552,15 +590,11 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
     FQ_CUDA(cudaMemcpyAsync(coef.p, coef_h.data(), sizeof(float2) * (size_t)nf * (k - 1),
                             cudaMemcpyHostToDevice, st));
     FQ_TRY((filter_coef<float, double>(op, R.p, d, corr.p, d, coef.p, k - 1, nf, nf, true, st)));
-    // span(S) = span(Xn, g_k(U) Xn_active) = span(Xn, corr_active): the filtered vector is
-    // g(omega) x + corr and its x part is already in span(Xn). Appending corr rather than the
-    // filtered vector avoids the cancellation (||corr|| ~ 1e-9 ||g x|| once converged) that
-    // would leave the orthonormalised basis non-orthogonal at the 1e-6 level.
-    FQ_CUDA(cudaMemcpyAsync(S.p, Xn.p, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
-    FQ_CUDA(cudaMemcpyAsync(S.p + (size_t)nb * d, corr.p, sizeof(double2) * nf * d,
+    // span(S) = span(Xn, g_k(U) Xn_active) = span(Xn, corr_active)
+    FQ_CUDA(cudaMemcpyAsync(S.p, Xn.p, sizeof(double2) * nk * d, cudaMemcpyDeviceToDevice, st));
+    FQ_CUDA(cudaMemcpyAsync(S.p + (size_t)nk * d, corr.p, sizeof(double2) * nf * d,
                             cudaMemcpyDeviceToDevice, st));
-    ns = nb + nf;
-    FQ_TRY(orthonormalize(ws, S.p, ns, d, st));
+    FQ_TRY(orthonormalize(ws, S.p, nk + nf, d, drop, &ns, st));
   }
   return FLOQUET_OK;
 }
