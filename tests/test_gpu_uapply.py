@@ -237,3 +237,30 @@ def test_filter_double_float_matches_oracle(L, k, phi, form):
     torch.cuda.synchronize()
     want = geosum.filter_acc(op, x, phi, k)
     assert _rel(from_dev(t_out), want) < 1e-14 * k * (L + 3)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("L", [13, 15, 18, 20])
+def test_every_launch_shape_matches_oracle(variant, L, monkeypatch):
+    # the autotuner may pick any launch shape (2, 3 or 4 passes per U); force each one
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    monkeypatch.setenv("FLOQUET_PASS_VARIANT", str(variant))
+    fq, op = _make(L, 1.0, 0.9045, 1.0, 800 + L)
+    X = inputs.random_states(1 << L, 3, 14)
+    want = op.apply_u_block(X)
+    for dt, sweep, tol in [(torch.complex128, None, 1e-13 * (L + 3)),
+                           (torch.complex64, None, 2e-7 * (L + 3)),
+                           (torch.complex128, floquet.C128_DF, 1e-14 * (L + 3))]:
+        t_in = to_dev(X, dt)
+        t_out = torch.empty_like(t_in)
+        fq.apply_u(t_in, t_out, sweep=sweep)
+        torch.cuda.synchronize()
+        assert _rel(from_dev(t_out, 1 << L), want) < tol, (dt, sweep)
+    # and the filter (last pass with the accumulate epilogue) in the same shape
+    x = inputs.complex_gaussian(1 << L, 15)
+    t_in = to_dev(x, torch.complex128)
+    t_out = torch.empty_like(t_in)
+    fq.filter_apply(0.3, 5, t_in, t_out, sweep=floquet.C128_DF)
+    torch.cuda.synchronize()
+    assert _rel(from_dev(t_out), geosum.filter_acc(op, x, 0.3, 5)) < 1e-13
