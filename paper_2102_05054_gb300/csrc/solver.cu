@@ -210,20 +210,10 @@ static int ks_filter(KS& s, int j) {
                                     s.vpp, true, s.st);
 }
 
-static int ks_expand(KS& s, int p) {
-  for (int j = p; j < s.m; ++j) {
-    FQ_TRY(ks_filter(s, j));
-    FQ_TRY(cgs2(s.ws, s.V.p, s.d, s.strideV(), j + 1, s.w.p, s.d, s.d, s.B,
-                s.H.p + (int64_t)j * s.ldh(), s.strideH(), s.V.p + (int64_t)(j + 1) * s.d,
-                s.strideV(), s.st));
-  }
-  return FLOQUET_OK;
-}
-
-// Ritz vectors X_b = V_b Y_b[:, :nx], then W = U X and (omega, resid) to host
-static int ks_ritz(KS& s, int nx, std::vector<double>& rq_host) {
+// Ritz vectors X_b = V_b[:, :n] Y_b[:, :nx], then W = U X and (omega, resid) to host
+static int ks_ritz(KS& s, int n, int nx, std::vector<double>& rq_host) {
   FQ_TRY(gemm_nn(s.V.p, s.d, s.strideV(), s.Y.p, s.m, (int64_t)s.m * s.m, s.X.p, s.d,
-                 s.d * nx, s.d, s.m, nx, s.B, s.st));
+                 s.d * nx, s.d, n, nx, s.B, s.st));
   FQ_TRY(apply_u<double>(s.op, s.X.p, s.W.p, s.B * nx, nx * s.vpp, s.st));
   FQ_TRY(rayleigh_residual(s.ws, s.X.p, s.W.p, s.d, s.B * nx, s.rq.p, s.st));
   rq_host.resize((size_t)3 * s.B * nx);
@@ -287,28 +277,30 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
   int p = 0;
   int restarts = 0;
   bool all_done = false;
-  for (;; ++restarts) {
-    FQ_TRY(ks_expand(s, p));
-    if (stats) stats->expansions += (m - p);
-    FQ_TRY(small_eig_batched(s.H.p, s.ldh(), s.strideH(), m, B, s.lam.p, m, s.Y.p, m,
+  // Convergence check on the current Krylov decomposition of dimension n (n <= m): Ritz
+  // pairs of H[:n, :n], Ritz estimates |beta_n| |e_n^T y|, and for problems with more than nev
+  // converged values the Ritz vectors, Rayleigh quotients, residuals and the completeness
+  // rule. Leaves nc[b] (converged prefix) and, in s.Y, the eigenvectors of H[:n, :n].
+  std::vector<int> nc(B, 0);
+  auto check = [&](int n) -> int {
+    FQ_TRY(small_eig_batched(s.H.p, s.ldh(), s.strideH(), n, B, s.lam.p, m, s.Y.p, m,
                              (int64_t)m * m, s.eigw.p, s.info.p, st));
     FQ_CUDA(cudaMemcpyAsync(lam_h.data(), s.lam.p, sizeof(double2) * B * m,
                             cudaMemcpyDeviceToHost, st));
-    FQ_CUDA(cudaMemcpy2DAsync(ylast.data(), sizeof(double2), s.Y.p + (m - 1),
+    FQ_CUDA(cudaMemcpy2DAsync(ylast.data(), sizeof(double2), s.Y.p + (n - 1),
                               sizeof(double2) * m, sizeof(double2), (size_t)B * m,
                               cudaMemcpyDeviceToHost, st));
     FQ_CUDA(cudaMemcpy2DAsync(beta_h.data(), sizeof(double2),
-                              s.H.p + (int64_t)(m - 1) * s.ldh() + m,
+                              s.H.p + (int64_t)(n - 1) * s.ldh() + n,
                               sizeof(double2) * s.strideH(), sizeof(double2), B,
                               cudaMemcpyDeviceToHost, st));
     FQ_CUDA(cudaStreamSynchronize(st));
     // converged prefix per problem
-    std::vector<int> nc(B, 0);
     int nx = 0;
     for (int b = 0; b < B; ++b) {
       const double beta = std::abs(cd(beta_h[b].x, beta_h[b].y));
       int c = 0;
-      while (c < m) {
+      while (c < n) {
         const cd th(lam_h[(size_t)b * m + c].x, lam_h[(size_t)b * m + c].y);
         const cd yl(ylast[(size_t)b * m + c].x, ylast[(size_t)b * m + c].y);
         if (beta * std::abs(yl) > tol * std::abs(th)) break;
@@ -318,7 +310,7 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
       if (!res[b].done && c > nev) nx = std::max(nx, c);
     }
     if (nx > 0) {
-      FQ_TRY(ks_ritz(s, nx, rq_h));
+      FQ_TRY(ks_ritz(s, n, nx, rq_h));
       for (int b = 0; b < B; ++b) {
         if (res[b].done || nc[b] <= nev) continue;
         std::vector<cd> om(nc[b]);
@@ -367,6 +359,33 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
         o.converged = true;
       }
     }
+    return FLOQUET_OK;
+  };
+
+  const int check_every = 16;
+  for (;; ++restarts) {
+    // expand p -> m, checking for convergence every check_every steps once the basis can
+    // hold nev + check_every Ritz pairs (the Krylov relation holds at every size)
+    bool done_early = false;
+    for (int j = p; j < m; ++j) {
+      FQ_TRY(ks_filter(s, j));
+      FQ_TRY(cgs2(s.ws, s.V.p, s.d, s.strideV(), j + 1, s.w.p, s.d, s.d, s.B,
+                  s.H.p + (int64_t)j * s.ldh(), s.strideH(), s.V.p + (int64_t)(j + 1) * s.d,
+                  s.strideV(), s.st));
+      if (stats) stats->expansions += 1;
+      const int n = j + 1;
+      if (n < m && n >= std::max(p + check_every, nev + check_every) && n % check_every == 0) {
+        FQ_TRY(check(n));
+        bool all = true;
+        for (int b = 0; b < B; ++b) all &= res[b].done;
+        if (all) {
+          done_early = true;
+          break;
+        }
+      }
+    }
+    if (!done_early) FQ_TRY(check(m));
+
     all_done = true;
     for (int b = 0; b < B; ++b) all_done &= res[b].done;
     if (all_done || restarts >= max_restarts) break;
