@@ -95,16 +95,29 @@ def _dist():
     return ws, rank, local
 
 
+def replica_seed(base_seed, rank):
+    """Disorder seed of the realisation a replica solves: independent problems per rank
+    (weak scaling, no data-path collective)."""
+    return base_seed + rank
+
+
+def max_over_ranks(value, device):
+    """Max of a per-rank float over the process group (the job's time is its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _cfg(args):
     from paper_2102_05054_gb300 import inputs
     c = dict(inputs.WORKLOADS[args.workload])
     if args.precision:
         c["precision"] = args.precision
     return c
-
-
-def _total_u_applications(cfg, stats_apps):
-    return stats_apps
 
 
 def run_gpu(args):
@@ -123,7 +136,7 @@ def run_gpu(args):
     prec = {"filter_fp32": floquet.FILTER_FP32, "fp64": floquet.FP64,
             "filter_df": floquet.FILTER_DF}[cfg["precision"]]
     d = 1 << L
-    h = inputs.disorder(L, cfg["W"], cfg["seed"] + rank)  # one realisation per replica
+    h = inputs.disorder(L, cfg["W"], replica_seed(cfg["seed"], rank))  # one per replica
     v0_host = inputs.start_vector(L)
     v0 = torch.from_numpy(v0_host).to(dev)
     evecs = torch.empty((nev, d), dtype=torch.complex128, device=dev)
@@ -177,11 +190,7 @@ def run_gpu(args):
     floquet.profile_enable(False)
     clocks = sampler.stop()
 
-    t_step = sum(times) / len(times)
-    if ws > 1:
-        t = torch.tensor([t_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(sum(times) / len(times), dev)
     if t_e2e is None:  # no warm-up: measure the end-to-end call now
         barrier()
         te = time.perf_counter()

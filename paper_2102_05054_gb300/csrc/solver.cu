@@ -374,7 +374,10 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
                   s.strideV(), s.st));
       if (stats) stats->expansions += 1;
       const int n = j + 1;
-      if (n < m && n >= std::max(p + check_every, nev + check_every) && n % check_every == 0) {
+      // (not for the FP32-filter form: its polish needs the full converged block as guard
+      // directions, which only the complete Krylov space provides)
+      if (precision != FLOQUET_FILTER_FP32 && n < m &&
+          n >= std::max(p + check_every, nev + check_every) && n % check_every == 0) {
         FQ_TRY(check(n));
         bool all = true;
         for (int b = 0; b < B; ++b) all &= res[b].done;

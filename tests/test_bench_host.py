@@ -1,0 +1,77 @@
+"""Host-side pieces of bench.py that need no GPU: the replica bookkeeping of the N > 1 path
+(run as two gloo ranks on the CPU) and the reference arm's JSON line."""
+
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t = bench.max_over_ranks(1.5 + rank, "cpu")
+    out.put((rank, t, bench.replica_seed(1, rank)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank_and_distinct_seeds():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [t for _, t, _ in res] == [2.5, 2.5]
+    assert res[0][2] != res[1][2]
+
+
+def _run_bench(extra_env=None, *args):
+    env = dict(os.environ)
+    env.update(extra_env or {})
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "kicked_ising_L10", "--ref-seconds", "0.2", "--warmup", "0",
+                        "--steps", "1", *args], capture_output=True, text=True, env=env,
+                       timeout=300)
+    return r
+
+
+def test_reference_arm_prints_one_json_line():
+    r = _run_bench()
+    assert r.returncode == 0, r.stderr
+    lines = [line for line in r.stdout.splitlines() if line.startswith("{")]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "higher_is_better",
+                "config", "cpu_baseline", "e2e"):
+        assert key in j
+    assert j["impl"] == "reference" and j["higher_is_better"] is False
+    assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_non_zero_ranks_exit_quietly():
+    r = _run_bench({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
+    assert r.returncode == 0
+    assert not [line for line in r.stdout.splitlines() if line.startswith("{")]
