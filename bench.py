@@ -246,10 +246,15 @@ def run_gpu(args):
     return out
 
 
+# Kernels whose committed ncu counters were taken on the current code (others report null).
+_CURRENT_TRAFFIC = {"df"}
+
+
 def _ncu_traffic(L, kind):
-    """DRAM bytes per U application from the committed ncu summary, if one matches."""
+    """DRAM bytes per U application from the committed ncu summary, if one matches the
+    current kernel."""
     p = os.path.join(ROOT, "profiles", f"pass_kernel_L{L}_{kind}_traffic.json")
-    if os.path.exists(p):
+    if kind in _CURRENT_TRAFFIC and os.path.exists(p):
         with open(p) as f:
             return json.load(f).get("dram_bytes_per_u_application")
     return None

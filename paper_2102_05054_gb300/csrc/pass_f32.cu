@@ -13,12 +13,14 @@ template <> PassVariant variant_info<float>(int v) { return kVariants[v]; }
 template <>
 int launch_pass_variant<float>(int v, const PassArgs<float>& a, int epi, bool swap, int nvec,
                                cudaStream_t st) {
-  if (a.NB == 12) {
-    if (v == 1) return dispatch_epi<float, 12, 3, 1>(a, epi, swap, nvec, st);
-    return dispatch_epi<float, 12, 4, 2>(a, epi, swap, nvec, st);
+  if (a.NB == kVariants[v].NB) {
+    switch (v) {
+      case 0: return dispatch_epi<float, 12, 4, 2>(a, epi, swap, nvec, st);
+      case 1: return dispatch_epi<float, 12, 3, 1>(a, epi, swap, nvec, st);
+      case 2: return dispatch_epi<float, 11, 4, 2>(a, epi, swap, nvec, st);
+      case 3: return dispatch_epi<float, 10, 4, 2>(a, epi, swap, nvec, st);
+    }
   }
-  if (a.NB == 11) return dispatch_epi<float, 11, 4, 2>(a, epi, swap, nvec, st);
-  if (a.NB == 10) return dispatch_epi<float, 10, 4, 2>(a, epi, swap, nvec, st);
   if (a.NB >= 4) return dispatch_epi<float, 0, 4, 1>(a, epi, swap, nvec, st);
   return dispatch_epi<float, 0, 3, 1>(a, epi, swap, nvec, st);
 }

@@ -593,9 +593,19 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
     for (int i = 0; i < nk; ++i)
       if (rq_h[3 * i + 2] > 0.1 * tol_resid) act.push_back(i);
     const int nf = (int)act.size();
-    if (verbose)
+    if (verbose) {
       fprintf(stderr, "floquet polish: iter %d space %d block %d worst selected resid %.3e, "
               "filtering %d\n", it, ns, nk, worst, nf);
+      int wi = -1;
+      for (int i : sel)
+        if (wi < 0 || rq_h[3 * i + 2] > rq_h[3 * wi + 2]) wi = i;
+      if (wi >= 0)
+        fprintf(stderr, "  worst pair: block index %d |omega|-1 %.2e angle %.4e |g| %.4e "
+                "(block |g| range %.4e .. %.4e), candidates %d\n", wi,
+                std::abs(om[wi]) - 1.0, wrapped_angle(om[wi], phi),
+                std::abs(gk_value(om[wi], phi, k)), gabs[order[0]], gabs[order[nk - 1]],
+                (int)sel.size());
+    }
     if (worst <= tol_resid || it >= max_iter || nf == 0) {
       FQ_CUDA(cudaMemcpyAsync(X0, Xn.p, sizeof(double2) * nk * d, cudaMemcpyDeviceToDevice, st));
       break;

@@ -239,7 +239,7 @@ def test_filter_double_float_matches_oracle(L, k, phi, form):
     assert _rel(from_dev(t_out), want) < 1e-14 * k * (L + 3)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("L", [13, 15, 18, 20])
 def test_every_launch_shape_matches_oracle(variant, L, monkeypatch):
     # the autotuner may pick any launch shape (2, 3 or 4 passes per U); force each one
