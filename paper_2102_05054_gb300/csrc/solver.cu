@@ -556,7 +556,13 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
     std::vector<int> order(ns);
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> gabs(ns);
-    for (int i = 0; i < ns; ++i) gabs[i] = std::abs(gk_value(cd(lam_h[i].x, lam_h[i].y), phi, k));
+    // Ritz values off the unit circle are mixtures (a converged pair with ||omega| - 1|
+    // ~ resid^2 / 2 is far closer to it); rank them after every value on the circle
+    for (int i = 0; i < ns; ++i) {
+      const cd l(lam_h[i].x, lam_h[i].y);
+      gabs[i] = std::abs(gk_value(l, phi, k));
+      if (std::fabs(std::abs(l) - 1.0) > 1e-8) gabs[i] *= 1e-6;
+    }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gabs[a] > gabs[b]; });
     order.resize(nk);
     for (int i = 0; i < nk; ++i)
@@ -570,12 +576,13 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
     FQ_CUDA(cudaStreamSynchronize(st));
     std::vector<cd> om(nk);
     for (int i = 0; i < nk; ++i) om[i] = cd(rq_h[3 * i], rq_h[3 * i + 1]);
-    // Rayleigh-Ritz over an extended space also yields values inside the unit disk (mixtures
-    // of correction directions); only values on the circle inside the main lobe are
-    // candidates.
+    // Rayleigh-Ritz over an extended space also yields mixtures of eigenvectors whose
+    // Rayleigh quotients sit inside the unit disk; an eigenpair with residual r has
+    // ||omega| - 1| ~ r^2 / 2, so only values within 1e-8 of the circle (residual below
+    // ~1e-4) inside the main lobe are candidates.
     std::vector<cd> om_c(nk);
     for (int i = 0; i < nk; ++i)
-      om_c[i] = std::fabs(std::abs(om[i]) - 1.0) < 1e-4 ? om[i] : cd(0.0, 0.0);
+      om_c[i] = std::fabs(std::abs(om[i]) - 1.0) < 1e-8 ? om[i] : cd(0.0, 0.0);
     const std::vector<int> sel = select_closest(om_c, phi, k, nev, true);
     double worst = sel.size() < (size_t)nev ? INFINITY : 0.0;
     for (int i : sel) worst = std::max(worst, rq_h[3 * i + 2]);
