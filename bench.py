@@ -216,7 +216,8 @@ def run_gpu(args):
             "data": "synthetic (seeded h_i ~ U[-1,1], complex-Gaussian start vector)",
             "config": {"workload": args.workload, "L": L, "J": inputs.J_DEFAULT,
                        "g": inputs.G_DEFAULT, "W": cfg["W"], "phi": phi, "k": k, "m": m,
-                       "nev": nev, "precision": cfg["precision"], "filter_form": "acc",
+                       "nev": nev, "precision": cfg["precision"],
+                       "filter_form": os.environ.get("FLOQUET_KRYLOV_FORM", "horner"),
                        "parallelism": f"replicas x{ws}",
                        "l2": "working set larger than L2 (Krylov basis 4 GiB) and a 256 MiB "
                              "buffer written between steps"},
@@ -230,7 +231,8 @@ def run_gpu(args):
                          "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4) if achieved else None,
                          "traffic": traffic, "kernel": "U application (pass_kernel x2)",
-                         "bytes_per_u_application": 4 * d * (8 if kind == "c64" else 16),
+                         "bytes_per_u_application": int(round(alg_bytes / u_apps)) if u_apps
+                         else None,
                          "u_applications": int(u_apps), "sweep_s": round(sweep_ms / 1e3, 3),
                          "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
             "gpu_launches": int(launches // max(1, args.steps)),

@@ -145,7 +145,8 @@ enum Epilogue {
   EPI_STORE = 0,        // dst = K_pass src
   EPI_PHASE = 1,        // dst = D K_pass src (last pass of U)
   EPI_PHASE_ACC = 2,    // dst = D K_pass src; acc += coef[j] * dst
-  EPI_PHASE_HORNER = 3  // dst = psi_in + z * D K_pass src (src = dst = acc)
+  EPI_PHASE_HORNER = 3  // dst = psi_in + (z D) K_pass src (src = dst = acc; z is folded into
+                        // the per-vector tab_lo)
 };
 
 // Everything a pass kernel needs, passed by value.
@@ -161,6 +162,7 @@ template <typename Real> struct PassArgs {
   int a;
   int64_t tab_lo_stride, tab_hi_stride;  // per problem
   int vec_per_prob;
+  int lo_by_vec;      // tab_lo holds one table per vector (Horner: z folded in) instead of per problem
   // accumulate / Horner epilogue
   cplx<Real>* acc;
   const cplx<Real>* coef;  // per vector: coef[vec * coef_stride + jstep]
@@ -170,10 +172,13 @@ template <typename Real> struct PassArgs {
 };
 
 // Launch shapes of the pass kernel that the autotuner chooses from, per sweep precision: the
-// tile of 2^NB amplitudes (the plan's pass structure follows from it) and 2^RB amplitudes
-// per thread.
+// tile of 2^NB amplitudes (the plan's pass structure follows from it), 2^RB amplitudes per
+// thread, the column bits later passes keep (0: the precision's default) and whether the
+// persistent pipelined kernel (pass_pipe.cuh) runs the passes it has been compiled for.
 struct PassVariant {
   int NB, RB;
+  int cols = 0;
+  bool pipe = false;
 };
 template <typename Real> int num_variants();
 template <typename Real> PassVariant variant_info(int v);
@@ -241,6 +246,8 @@ struct floquet_op {
   void* acc = nullptr;
   void* psi_in_copy = nullptr;
   size_t work_bytes = 0;
+  void* zlo = nullptr;  // Horner: per-vector tab_lo with the filter's z folded in
+  size_t zlo_bytes = 0;
   void* coef = nullptr;
   size_t coef_bytes = 0;
   double coef_phi = 0;

@@ -5,7 +5,14 @@ namespace fq {
 
 // {tile bits, register bits}: large tiles for large states, smaller tiles so that mid-size
 // states (L = 12..18) still give every SM a few CTAs per pass.
-static const PassVariant kVariants[] = {{11, 3}, {12, 4}, {10, 3}, {9, 3}, {11, 3}};
+// Shapes 4 and 5 keep two column bits in later passes (64-byte row segments), so that L = 20
+// (2^11 tiles) and L = 18 (2^10 tiles) take two passes, and run them with the pipelined kernel.
+static const PassVariant kVariants[] = {{11, 3}, {12, 4}, {10, 3}, {9, 3},
+                                        {11, 3, 2, true}, {10, 3, 2, true}};
+
+// pass_df_pipe.cu: launches the pipelined kernel if it is compiled for this pass
+bool launch_pass_pipe_df(int NB, const PassArgs<dfloat>& a, int epi, bool swap, int nvec,
+                         cudaStream_t st, int* rc);
 
 template <> int num_variants<dfloat>() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
 template <> PassVariant variant_info<dfloat>(int v) { return kVariants[v]; }
@@ -13,16 +20,16 @@ template <> PassVariant variant_info<dfloat>(int v) { return kVariants[v]; }
 template <>
 int launch_pass_variant<dfloat>(int v, const PassArgs<dfloat>& a, int epi, bool swap, int nvec,
                                cudaStream_t st) {
-  // the shape's own tile uses its compile-time kernel; a smaller single-pass tile (L below
-  // the shape's tile bits) uses the generic one. Shape 4 is shape 0 limited to 64 registers
-  // (four CTAs per SM: 512 tiles of an L = 20 pass then fit one wave).
+  // the shape's own tile uses its compile-time kernel (the pipelined one where compiled); a
+  // smaller single-pass tile (L below the shape's tile bits) uses the generic one
   if (a.NB == kVariants[v].NB) {
+    int rc = FLOQUET_OK;
+    if (kVariants[v].pipe && launch_pass_pipe_df(a.NB, a, epi, swap, nvec, st, &rc)) return rc;
     switch (v) {
-      case 0: return dispatch_epi<dfloat, 11, 3, 3>(a, epi, swap, nvec, st);
+      case 0: case 4: return dispatch_epi<dfloat, 11, 3, 3>(a, epi, swap, nvec, st);
       case 1: return dispatch_epi<dfloat, 12, 4, 2>(a, epi, swap, nvec, st);
-      case 2: return dispatch_epi<dfloat, 10, 3, 3>(a, epi, swap, nvec, st);
+      case 2: case 5: return dispatch_epi<dfloat, 10, 3, 3>(a, epi, swap, nvec, st);
       case 3: return dispatch_epi<dfloat, 9, 3, 3>(a, epi, swap, nvec, st);
-      case 4: return dispatch_epi<dfloat, 11, 3, 4>(a, epi, swap, nvec, st);
     }
   }
   return dispatch_epi<dfloat, 0, 3, 1>(a, epi, swap, nvec, st);

@@ -223,13 +223,12 @@ __global__ void __launch_bounds__(pass_max_threads<NBT, RB>(), MINB)
     return;
   }
   const int64_t prob = vec / A.vec_per_prob;
-  const C* __restrict__ tlo = A.tab_lo + prob * A.tab_lo_stride;
+  const C* __restrict__ tlo = A.tab_lo + (A.lo_by_vec ? vec : prob) * A.tab_lo_stride;
   const C* __restrict__ thi = A.tab_hi + prob * A.tab_hi_stride;
   const uint32_t lomask = (1u << A.a) - 1u;
   const int am1 = A.a - 1;
   C cj;
   if (EPI == EPI_PHASE_ACC) cj = A.coef[vec * A.coef_stride + A.jstep];
-  if (EPI == EPI_PHASE_HORNER) cj = A.coef[vec * A.coef_stride];
   C* __restrict__ acc = A.acc + vec * A.d;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -243,8 +242,8 @@ __global__ void __launch_bounds__(pass_max_threads<NBT, RB>(), MINB)
       if (EPI == EPI_PHASE_ACC) {
         dst[s] = val;
         acc[s] = zfma(cj, val, o);
-      } else {  // Horner: dst (= acc) = psi_in + z * U acc
-        dst[s] = zfma(cj, val, o);
+      } else {  // Horner: dst (= acc) = psi_in + z U acc, z folded into the table
+        dst[s] = zfma(p, v[r], o);
       }
     }
   }

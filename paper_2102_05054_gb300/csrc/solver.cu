@@ -144,9 +144,10 @@ struct KS {
   DevBuf<double2> V, V2, H, H2, w, lam, Y, Q, Bp, Tmp, eigw, X, W, R, Xs;
   DevBuf<double> rq;
   DevBuf<int> info;
-  DevBuf<double2> coef64;
+  DevBuf<double2> coef64;  // accumulate form: z_b^j, j < k, per problem
   DevBuf<float2> coef32;
   DevBuf<float4> coefdf;
+  bool horner = true;      // Horner form: only z_b per problem (the first entry of each row)
   int64_t strideV() const { return d * (m + 1); }
   int64_t ldh() const { return m + 1; }
   int64_t strideH() const { return (int64_t)(m + 1) * m; }
@@ -169,12 +170,17 @@ static int ks_alloc(KS& s) {
   FQ_TRY(s.X.alloc(B * d * m));
   FQ_TRY(s.W.alloc(B * d * m));
   FQ_TRY(s.rq.alloc(B * m * 3));
-  // filter coefficients z_b^j = exp(-i j phi_b), float64 on the host
-  std::vector<double2> c64((size_t)B * s.k);
+  // filter coefficients z_b^j = exp(-i j phi_b), float64 on the host: j < k for the
+  // accumulate form, j = 1 only for the Horner form (the default; FLOQUET_KRYLOV_FORM=acc
+  // selects the accumulate form)
+  const char* form = getenv("FLOQUET_KRYLOV_FORM");
+  s.horner = !(form && strcmp(form, "acc") == 0);
+  const int64_t nc = s.horner ? 1 : s.k;
+  std::vector<double2> c64((size_t)B * nc);
   for (size_t b = 0; b < B; ++b)
-    for (int64_t j = 0; j < s.k; ++j) {
-      const double a = -s.phis[b] * (double)j;
-      c64[b * s.k + j] = make_double2(cos(a), sin(a));
+    for (int64_t j = 0; j < nc; ++j) {
+      const double a = -s.phis[b] * (double)(s.horner ? 1 : j);
+      c64[b * nc + j] = make_double2(cos(a), sin(a));
     }
   if (s.precision == FLOQUET_FP64) {
     FQ_TRY(s.coef64.alloc(c64.size()));
@@ -200,6 +206,16 @@ static int ks_alloc(KS& s) {
 // w_b = g_k(U_b) V_b[:, j]
 static int ks_filter(KS& s, int j) {
   const double2* in = s.V.p + (int64_t)j * s.d;
+  if (s.horner) {
+    if (s.precision == FLOQUET_FP64)
+      return filter_horner<double, double>(s.op, in, s.strideV(), s.w.p, s.d, s.coef64.p, s.k,
+                                           s.B, s.vpp, true, s.st);
+    if (s.precision == FLOQUET_FILTER_DF)
+      return filter_horner<dfloat, double>(s.op, in, s.strideV(), s.w.p, s.d, s.coefdf.p, s.k,
+                                           s.B, s.vpp, true, s.st);
+    return filter_horner<float, double>(s.op, in, s.strideV(), s.w.p, s.d, s.coef32.p, s.k,
+                                        s.B, s.vpp, true, s.st);
+  }
   if (s.precision == FLOQUET_FP64)
     return filter_coef<double, double>(s.op, in, s.strideV(), s.w.p, s.d, s.coef64.p, s.k, s.B,
                                        s.vpp, true, s.st);

@@ -293,7 +293,8 @@ template <typename Real> static int min_cols() { return sizeof(cplx<Real>) == 8 
 template <typename Real> static void set_variant(floquet_op* op, int v) {
   const int t = sweep_dtype<Real>();
   op->variant[t] = v;
-  op->plan[t] = make_plan(op->L, variant_info<Real>(v).NB, min_cols<Real>());
+  const PassVariant pv = variant_info<Real>(v);
+  op->plan[t] = make_plan(op->L, pv.NB, pv.cols > 0 ? pv.cols : min_cols<Real>());
 }
 
 int op_init(floquet_op* op, int L, double J, double g, const double* h, int nprob) {
@@ -397,6 +398,7 @@ void op_free(floquet_op* op) {
   cudaFree(op->work);
   cudaFree(op->acc);
   cudaFree(op->psi_in_copy);
+  cudaFree(op->zlo);
   cudaFree(op->coef);
 }
 
@@ -418,7 +420,8 @@ template <> const float4* thi_of<dfloat>(const floquet_op* op) { return op->tabs
 template <typename Real>
 static int u_passes(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int nvec,
                     int vec_per_prob, int epi, cplx<Real>* acc, const cplx<Real>* coef,
-                    int64_t coef_stride, int jstep, const cplx<Real>* psi_in, cudaStream_t st) {
+                    int64_t coef_stride, int jstep, const cplx<Real>* psi_in, cudaStream_t st,
+                    const cplx<Real>* lo_per_vec = nullptr) {
   const Plan& pl = plan_of<Real>(op);
   const int np = (int)pl.passes.size();
   for (int i = 0; i < np; ++i) {
@@ -433,6 +436,10 @@ static int u_passes(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int n
       a.coef_stride = coef_stride;
       a.jstep = jstep;
       a.psi_in = psi_in;
+      if (lo_per_vec) {  // one tab_lo per vector (Horner, z folded in)
+        a.tab_lo = lo_per_vec;
+        a.lo_by_vec = 1;
+      }
     }
     FQ_TRY(launch_pass_variant<Real>(op->variant[sweep_dtype<Real>()], a,
                                      last ? epi : EPI_STORE, op->swap, nvec, st));
@@ -635,6 +642,18 @@ int filter_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio
   return launch_convert_strided<Real, Rio>(acc, out, out_stride, d, nvec, st);
 }
 
+// out[v * lo_n + j] = zs[v] * tab_lo[(v / vpp) * lo_n + j], the product formed in float64
+template <typename Real>
+__global__ void scale_lo_kernel(const cplx<Real>* __restrict__ tlo, int64_t lo_n, int vpp,
+                                const cplx<Real>* __restrict__ zs, cplx<Real>* __restrict__ out,
+                                int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / lo_n, j = i - v * lo_n;
+    out[i] = from_d2<Real>(cmul(to_d2(zs[v]), to_d2(tlo[(v / vpp) * lo_n + j])));
+  }
+}
+
 template <typename Real, typename Rio>
 int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio>* out,
                   int64_t out_stride, const cplx<Real>* zs, int64_t k, int nvec,
@@ -645,12 +664,33 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
   FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
   C* pin = reinterpret_cast<C*>(op->psi_in_copy);
   C* acc = reinterpret_cast<C*>(op->acc);
+  // z folded into a per-vector copy of tab_lo, so the Horner epilogue is one complex
+  // multiply-add; the buffer outlives the call because cached graphs hold its address
+  const int64_t lo_n = op->tabs.lo_n;
+  const size_t zbytes = (size_t)nvec * lo_n * sizeof(C);
+  if (op->zlo_bytes < zbytes) {
+    destroy_graphs(op);
+    cudaFree(op->zlo);
+    op->zlo = nullptr;
+    op->zlo_bytes = 0;
+    if (cudaMalloc(&op->zlo, zbytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("filter workspace: cudaMalloc of %zu bytes failed", zbytes);
+      return FLOQUET_ENOMEM;
+    }
+    op->zlo_bytes = zbytes;
+  }
+  C* zlo = reinterpret_cast<C*>(op->zlo);
+  scale_lo_kernel<Real><<<grid_for(nvec * lo_n, 256), 256, 0, st>>>(
+      tlo_of<Real>(op), lo_n, vec_per_prob, zs, zlo, nvec * lo_n);
+  count_launch();
+  FQ_CHECK_LAUNCH();
   FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, pin, acc, nullptr, 0, d, nvec, st)));
   const int np = (int)plan_of<Real>(op).passes.size();
   auto body = [&](cudaStream_t s) -> int {
     for (int64_t j = 1; j < k; ++j)
-      FQ_TRY(u_passes<Real>(op, acc, acc, nvec, vec_per_prob, EPI_PHASE_HORNER, nullptr, zs, 1,
-                            0, pin, s));
+      FQ_TRY(u_passes<Real>(op, acc, acc, nvec, vec_per_prob, EPI_PHASE_HORNER, nullptr,
+                            nullptr, 0, 0, pin, s, zlo));
     return FLOQUET_OK;
   };
   if (k > 1)

@@ -239,7 +239,7 @@ def test_filter_double_float_matches_oracle(L, k, phi, form):
     assert _rel(from_dev(t_out), want) < 1e-14 * k * (L + 3)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("L", [13, 15, 18, 20])
 def test_every_launch_shape_matches_oracle(variant, L, monkeypatch):
     # the autotuner may pick any launch shape (2, 3 or 4 passes per U); force each one
@@ -264,3 +264,35 @@ def test_every_launch_shape_matches_oracle(variant, L, monkeypatch):
     fq.filter_apply(0.3, 5, t_in, t_out, sweep=floquet.C128_DF)
     torch.cuda.synchronize()
     assert _rel(from_dev(t_out), geosum.filter_acc(op, x, 0.3, 5)) < 1e-13
+
+
+@pytest.mark.parametrize("variant,L", [(4, 18), (4, 19), (4, 20), (4, 21),
+                                       (5, 16), (5, 17), (5, 18), (5, 19)])
+@pytest.mark.parametrize("g", [0.4, 0.9045])   # tan and cot forms of the butterfly
+def test_pipelined_double_float_passes_match_oracle(variant, L, g, monkeypatch):
+    # double-float shapes 4 and 5 run the persistent cp.async-pipelined pass kernel for the
+    # first pass and for later passes with 2-4 column bits (L = 21 and 19 add a third pass
+    # that falls back to the one-tile-per-CTA kernel); several vectors, in place, and every
+    # epilogue (plain phase, accumulate, Horner)
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    monkeypatch.setenv("FLOQUET_PASS_VARIANT", str(variant))
+    fq, op = _make(L, 1.0, g, 1.0, 900 + L)
+    X = inputs.random_states(1 << L, 3, 16)
+    want = op.apply_u_block(X)
+    t = to_dev(X, torch.complex128)
+    t_out = torch.empty_like(t)
+    fq.apply_u(t, t_out, sweep=floquet.C128_DF)
+    fq.apply_u(t, t, sweep=floquet.C128_DF)  # in place
+    torch.cuda.synchronize()
+    assert _rel(from_dev(t_out, 1 << L), want) < 1e-14 * (L + 3)
+    assert _rel(from_dev(t, 1 << L), want) < 1e-14 * (L + 3)
+    Y = inputs.random_states(1 << L, 2, 17)
+    for form in (floquet.FORM_ACC, floquet.FORM_HORNER):
+        t_in = to_dev(Y, torch.complex128)
+        t_out = torch.empty_like(t_in)
+        fq.filter_apply(1.1, 5, t_in, t_out, form=form, sweep=floquet.C128_DF)
+        torch.cuda.synchronize()
+        got = from_dev(t_out, 1 << L)
+        for j in range(2):
+            assert _rel(got[:, j], geosum.filter_acc(op, Y[:, j], 1.1, 5)) < 1e-13, form
