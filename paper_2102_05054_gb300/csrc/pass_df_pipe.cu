@@ -16,11 +16,11 @@ static bool pipe_df(const PassArgs<dfloat>& a, int epi, bool swap, int nvec, cud
          pipe_launch_later<dfloat, NB, RB, 4>(a, epi, swap, nvec, st, rc);
 }
 
-bool launch_pass_pipe_df(int NB, const PassArgs<dfloat>& a, int epi, bool swap, int nvec,
-                         cudaStream_t st, int* rc) {
+bool launch_pass_pipe_df(int NB, int RB, const PassArgs<dfloat>& a, int epi, bool swap,
+                         int nvec, cudaStream_t st, int* rc) {
   if (a.NB != NB) return false;
-  if (NB == 11) return pipe_df<11, 3>(a, epi, swap, nvec, st, rc);
-  if (NB == 10) return pipe_df<10, 3>(a, epi, swap, nvec, st, rc);
+  if (NB == 11 && RB == 3) return pipe_df<11, 3>(a, epi, swap, nvec, st, rc);
+  if (NB == 10 && RB == 3) return pipe_df<10, 3>(a, epi, swap, nvec, st, rc);
   return false;
 }
 

@@ -196,10 +196,9 @@ __global__ void __launch_bounds__(1 << (NB - RB), MINB)
   cp_async_wait<0>();
 }
 
-// CTAs of one pipelined kernel that fit on the device at once (cached per instantiation).
+// CTAs of one pipelined kernel that fit on the device at once (the caller caches it per
+// kernel instantiation).
 template <typename K> static int pipe_resident_ctas(K kernel, int threads, size_t smem) {
-  static int cached = 0;
-  if (cached > 0) return cached;
   int dev = 0, nsm = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -209,21 +208,25 @@ template <typename K> static int pipe_resident_ctas(K kernel, int threads, size_
     cudaGetLastError();
     return 0;
   }
-  cached = nsm * per_sm;
-  return cached;
+  return nsm * per_sm;
 }
 
 // Resident CTAs per SM the launch bounds ask for: 768 threads per SM for the plain passes,
-// 512 when the epilogue keeps a second register copy of the tile (accumulator or psi_in).
-template <int EPI, int THREADS> constexpr int pipe_min_blocks() {
-  return ((EPI == EPI_PHASE_ACC || EPI == EPI_PHASE_HORNER) ? 512 : 768) / THREADS;
+// 512 when the epilogue keeps a second register copy of the tile (accumulator or psi_in),
+// 1024 for four amplitudes per thread; never more than the shared memory holds.
+template <int EPI, int THREADS, int RB, size_t SMEM> constexpr int pipe_min_blocks() {
+  constexpr int want = (RB <= 2 ? 1024
+                        : (EPI == EPI_PHASE_ACC || EPI == EPI_PHASE_HORNER) ? 512 : 768) /
+                       THREADS;
+  constexpr int fit = (int)((227 * 1024) / (SMEM + 1024));
+  return want < 1 ? 1 : (want < fit ? want : (fit < 1 ? 1 : fit));
 }
 
 template <typename Real, int NB, int RB, int KF, int EPI, bool SWAP>
 static int launch_pipe_t(const PassArgs<Real>& a, int nvec, cudaStream_t st) {
   constexpr int threads = 1 << (NB - RB);
   constexpr size_t smem = 2 * (size_t)((1 << NB) + (1 << (NB - RB))) * sizeof(cplx<Real>);
-  auto kernel = pass_pipe_kernel<Real, NB, RB, KF, EPI, SWAP, pipe_min_blocks<EPI, threads>()>;
+  auto kernel = pass_pipe_kernel<Real, NB, RB, KF, EPI, SWAP, pipe_min_blocks<EPI, threads, RB, smem>()>;
   if (smem > 48 * 1024) {
     // set once per instantiation, outside any stream capture (the autotuner launches every
     // shape before a filter graph is captured)
@@ -239,7 +242,8 @@ static int launch_pipe_t(const PassArgs<Real>& a, int nvec, cudaStream_t st) {
     set_error("launch_pass: grid too large (nvec %d)", nvec);
     return FLOQUET_EINVAL;
   }
-  const int resident = pipe_resident_ctas(kernel, threads, smem);
+  static int resident = 0;  // one value per instantiation
+  if (resident < 1) resident = pipe_resident_ctas(kernel, threads, smem);
   if (resident < 1) {
     set_error("launch_pass: occupancy query failed for the pipelined pass kernel");
     return FLOQUET_ECUDA;
