@@ -40,6 +40,30 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+# FP32 pipe: 152 SMs x 128 lanes, one FP32 instruction (FADD, FMUL or FFMA) per lane per clock
+N_SM, FP32_LANES = 152, 128
+
+
+def _fp32_peak_tops():
+    """FP32 instructions per second at the maximum SM clock (units x clock)."""
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return N_SM * FP32_LANES * mhz * 1e6 / 1e12, mhz
+
+
+def df_instr_per_amplitude(L, form):
+    """Algorithmic FP32 instructions per amplitude of one double-float U application: each
+    kicked qubit gives two real outputs per amplitude, each an error-free x + tau*y (12 FP32
+    instructions: exact product 2, two-sum 6, low-order terms 4); the epilogue is one
+    double-float complex product for the phase (44) and, for the Horner form, one complex
+    multiply-add (60) or, for the accumulate form, a second product plus the multiply-add
+    (104)."""
+    return 24 * L + (104 if form == "horner" else 148)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -203,10 +227,35 @@ def run_gpu(args):
     kind = {floquet.FILTER_FP32: "c64", floquet.FP64: "c128", floquet.FILTER_DF: "df"}[prec]
     sweep_ms, u_apps, alg_bytes = prof[kind]
     hbm, peak_kind = _peaks()
+    form = os.environ.get("FLOQUET_KRYLOV_FORM", "horner")
     out = None
     if rank == 0:
         achieved = alg_bytes / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
         traffic = _ncu_traffic(L, kind)
+        hbm_view = {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+                    "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4) if achieved else None,
+                    "traffic": traffic,
+                    "bytes_per_u_application": int(round(alg_bytes / u_apps)) if u_apps
+                    else None,
+                    "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+        if kind == "df" and sweep_ms > 0:
+            # the double-float sweep is bound by the FP32 pipe: algorithmic FP32 instructions
+            # per U application against the FP32 issue rate at the maximum clock
+            peak_t, mhz = _fp32_peak_tops()
+            ipa = df_instr_per_amplitude(L, form)
+            ach_t = ipa * d * u_apps / (sweep_ms / 1e3) / 1e12
+            roofline = {"bound": "alu", "achieved": round(ach_t, 2), "peak": round(peak_t, 2),
+                        "unit": "T FP32 instr/s", "frac": round(ach_t / peak_t, 4),
+                        "traffic": traffic, "kernel": "U application (pass_pipe_kernel x2)",
+                        "fp32_instr_per_amplitude": ipa, "u_applications": int(u_apps),
+                        "sweep_s": round(sweep_ms / 1e3, 3),
+                        "peak_source": f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x "
+                                       f"{mhz:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)",
+                        "hbm_view": hbm_view}
+        else:
+            roofline = dict(hbm_view, kernel="U application (pass kernels)",
+                            u_applications=int(u_apps), sweep_s=round(sweep_ms / 1e3, 3))
         out = {
             "metric": METRIC, "value": round(t_step, 4), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 2),
@@ -227,14 +276,7 @@ def run_gpu(args):
                     "h2d_bytes_per_step": int(d * 16 + L * 8),
                     "d2h_bytes_per_step": int(nev * d * 16 + nev * 24),
                     "status": rc_e, "n_conv": nconv_e},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
-                         "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4) if achieved else None,
-                         "traffic": traffic, "kernel": "U application (pass_kernel x2)",
-                         "bytes_per_u_application": int(round(alg_bytes / u_apps)) if u_apps
-                         else None,
-                         "u_applications": int(u_apps), "sweep_s": round(sweep_ms / 1e3, 3),
-                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "roofline": roofline,
             "gpu_launches": int(launches // max(1, args.steps)),
             "clocks": clocks,
         }
@@ -255,7 +297,8 @@ _CURRENT_TRAFFIC = {"df"}
 def _ncu_traffic(L, kind):
     """DRAM bytes per U application from the committed ncu summary, if one matches the
     current kernel."""
-    p = os.path.join(ROOT, "profiles", f"pass_kernel_L{L}_{kind}_traffic.json")
+    name = "pass_pipe_kernel" if kind == "df" else "pass_kernel"
+    p = os.path.join(ROOT, "profiles", f"{name}_L{L}_{kind}_traffic.json")
     if kind in _CURRENT_TRAFFIC and os.path.exists(p):
         with open(p) as f:
             return json.load(f).get("dram_bytes_per_u_application")
