@@ -460,3 +460,32 @@ void floquet_reset_launch_count(void) { reset_launch_count(); }
 const char* floquet_last_error(void) { return get_error(); }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ parameter rule (Secs. 3-4)
+
+extern "C" int floquet_suggest_params(int L, int nev, int max_m, int64_t* k, int* m) {
+  if (L < 3 || L > 24 || nev < 1 || !k || !m) {
+    set_error("floquet_suggest_params: need 3 <= L <= 24, nev >= 1 and output pointers");
+    return FLOQUET_EINVAL;
+  }
+  const int64_t d = (int64_t)1 << L;
+  const int64_t cap = std::min<int64_t>(max_m, d - 1);
+  if ((int64_t)2 * nev + 1 > cap) {
+    set_error("floquet_suggest_params: 2 nev + 1 = %d exceeds min(max_m, d - 1) = %lld",
+              2 * nev + 1, (long long)cap);
+    return FLOQUET_EINVAL;
+  }
+  // floor(2^(L/2 + 1)) = integer square root of 2^(L + 2)
+  const int64_t sq = (int64_t)1 << (L + 2);
+  int64_t r = (int64_t)std::sqrt((double)sq);
+  while (r * r > sq) --r;
+  while ((r + 1) * (r + 1) <= sq) ++r;
+  int64_t mm = std::max<int64_t>(r, (int64_t)2 * nev + 1);
+  mm = std::min<int64_t>(mm, cap);
+  // round(2^(L+3) / (5 m)) = floor((2^(L+4) + 5 m) / (10 m))
+  int64_t kk = (((int64_t)1 << (L + 4)) + 5 * mm) / (10 * mm);
+  if (kk < 2) kk = 2;
+  *k = kk;
+  *m = (int)mm;
+  return FLOQUET_OK;
+}

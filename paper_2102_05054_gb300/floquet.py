@@ -48,6 +48,8 @@ SIGNATURES = {
     "floquet_profile_enable": (_c_int, [_c_int]),
     "floquet_profile_read": (_c_int, [_dptr, ctypes.POINTER(_c_int64), _dptr]),
     "floquet_launch_count": (_c_int64, []),
+    "floquet_suggest_params": (_c_int, [_c_int, _c_int, _c_int, ctypes.POINTER(_c_int64),
+                                        ctypes.POINTER(_c_int)]),
     "floquet_reset_launch_count": (None, []),
     "floquet_last_error": (ctypes.c_char_p, []),
 }
@@ -261,3 +263,13 @@ def launch_count():
 
 def reset_launch_count():
     lib().floquet_reset_launch_count()
+
+
+def suggest_params(L, nev, max_m=512):
+    """(k, m) by the paper's rule (Secs. 3-4): m = max(floor(2^(L/2+1)), 2 nev + 1) capped at
+    min(max_m, d - 1), k = round(0.8 * 2^(L+1) / m). Host only."""
+    k = _c_int64(0)
+    m = _c_int(0)
+    _check(lib().floquet_suggest_params(int(L), int(nev), int(max_m), ctypes.byref(k),
+                                        ctypes.byref(m)), "floquet_suggest_params")
+    return int(k.value), int(m.value)

@@ -77,3 +77,23 @@ def test_calls_reject_null_handles(lib):
 def test_launch_counter_resets(lib):
     lib.floquet_reset_launch_count()
     assert lib.floquet_launch_count() == 0
+
+
+def test_suggest_params_matches_oracle(lib):
+    # the paper's (k, n_cv) rule: the C ABI (integer arithmetic) against the oracle (the
+    # formula in floating point); no GPU needed
+    from oracle import krylov
+    from paper_2102_05054_gb300 import floquet
+    for L in range(3, 25):
+        for nev in (1, 2, 5, 10, 50, 100, 200):
+            for max_m in (512, 300, 64):
+                try:
+                    want = krylov.paper_params(L, nev, max_m)
+                except ValueError:
+                    k = ctypes.c_int64()
+                    m = ctypes.c_int()
+                    assert lib.floquet_suggest_params(L, nev, max_m, ctypes.byref(k),
+                                                      ctypes.byref(m)) == floquet.EINVAL
+                    continue
+                assert floquet.suggest_params(L, nev, max_m) == want, (L, nev, max_m)
+    assert lib.floquet_suggest_params(2, 1, 512, None, None) == floquet.EINVAL

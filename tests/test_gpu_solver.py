@@ -188,3 +188,16 @@ def test_arnoldi_eigs_double_float_special_case_g0_L16():
     want = lam[krylov.select_closest(lam, phi, nev)]
     assert rc == 0 and nconv == nev
     assert np.abs(om - want).max() < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_arnoldi_eigs_with_paper_params_L12(precision):
+    # filter length and Krylov dimension from the paper's rule (floquet_suggest_params):
+    # L = 12, nev = 24 gives m = 128, k = 51 terms
+    from paper_2102_05054_gb300 import floquet
+    k, m = floquet.suggest_params(12, 24)
+    assert (k, m) == (51, 128)
+    om, res, nconv, rc, X, op = _solve(12, 1.0, 0.9045, 1.0, 6, 0.4, k, 24, m,
+                                       precision=precision)
+    assert rc == 0 and nconv == 24
+    _check_against_dense(om, res, X, op, 0.4, 24)

@@ -297,3 +297,30 @@ def test_pipelined_double_float_passes_match_oracle(variant, L, g, monkeypatch):
         got = from_dev(t_out, 1 << L)
         for j in range(2):
             assert _rel(got[:, j], geosum.filter_acc(op, Y[:, j], 1.1, 5)) < 1e-13, form
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("L", [22, 24])
+def test_maximum_sizes_match_oracle(L):
+    # the largest states the library accepts (L <= 24: 256 MiB per complex128 state), three
+    # or more passes per U with the autotuned shapes; every sweep precision and the Horner
+    # filter in double-float
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    fq, op = _make(L, 1.0, 0.9045, 1.0, 1000 + L)
+    x = inputs.complex_gaussian(1 << L, 18)
+    want = op.apply_u(x)
+    for dt, sweep, tol in [(torch.complex128, None, 1e-13 * (L + 3)),
+                           (torch.complex64, None, 2e-7 * (L + 3)),
+                           (torch.complex128, floquet.C128_DF, 1e-14 * (L + 3))]:
+        t_in = to_dev(x, dt)
+        t_out = torch.empty_like(t_in)
+        fq.apply_u(t_in, t_out, sweep=sweep)
+        torch.cuda.synchronize()
+        assert _rel(from_dev(t_out), want) < tol, (dt, sweep)
+        del t_in, t_out
+    t_in = to_dev(x, torch.complex128)
+    t_out = torch.empty_like(t_in)
+    fq.filter_apply(0.7, 3, t_in, t_out, form=floquet.FORM_HORNER, sweep=floquet.C128_DF)
+    torch.cuda.synchronize()
+    assert _rel(from_dev(t_out), geosum.filter_acc(op, x, 0.7, 3)) < 1e-13

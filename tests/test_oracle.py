@@ -161,7 +161,7 @@ def test_gk_paper_facts(k):
 
 
 def test_lobe_count_statistics():
-    # 2d/k eigenvalues on the outer lobe on average (Sec. 3); across targets the mean count
+    # 2d/k eigenvalues on the outer lobe on average (Sec. 2); across targets the mean count
     # over 16 targets must be close to 2d/k.
     L, k = 10, 32
     op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 11))
@@ -183,7 +183,7 @@ def test_filter_closed_form_on_exact_eigenvectors():
 
 
 def test_filter_peaks_at_target_eigenvalue():
-    # Sec. 3: the phase factor rotates the target to 1, where |g_k| peaks at the number of
+    # Sec. 2: the phase factor rotates the target to 1, where |g_k| peaks at the number of
     # terms. Choose phi = arg(omega) for an exact eigenvalue: g_k(U) v = k v.
     L, k = 7, 23
     op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 23))
@@ -349,3 +349,25 @@ def test_planted_single_gram_schmidt_pass_is_caught(monkeypatch):
     monkeypatch.setattr(krylov, "cgs2", cgs1)
     with pytest.raises(AssertionError):
         test_arnoldi_relation()
+
+
+def test_paper_params_pins():
+    # Sec. 4 fixes n_cv = floor(2^(L/2+1)) and k = 0.8 * 2^(L+1) / n_cv; for even L the
+    # Krylov dimension is a power of two, and in every case the Krylov dimension is about
+    # 80 % of the outer-lobe count 2d/k and more than twice the number of wanted pairs
+    assert krylov.paper_params(12, 50) == (51, 128)    # 0.8 * 8192 / 128 = 51.2
+    assert krylov.paper_params(14, 50) == (102, 256)   # 0.8 * 32768 / 256 = 102.4
+    assert krylov.paper_params(16, 50) == (205, 512)   # 0.8 * 131072 / 512 = 204.8
+    assert krylov.paper_params(13, 10) == (72, 181)    # floor(2^7.5) = 181
+    for L in range(6, 25):
+        for nev in (1, 10, 50, 100):
+            if 2 * nev + 1 > min(512, (1 << L) - 1):
+                with pytest.raises(ValueError):
+                    krylov.paper_params(L, nev)
+                continue
+            k, m = krylov.paper_params(L, nev)
+            assert m > 2 * nev and m <= 512
+            lobe = 2 * (1 << L) / k
+            assert abs(m / lobe - 0.8) < 0.8 * (0.5 / k) + 1e-12
+            if L % 2 == 0 and 2 ** (L // 2 + 1) <= 512 and 2 ** (L // 2 + 1) > 2 * nev:
+                assert m == 2 ** (L // 2 + 1)
