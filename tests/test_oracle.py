@@ -371,3 +371,88 @@ def test_paper_params_pins():
             assert abs(m / lobe - 0.8) < 0.8 * (0.5 / k) + 1e-12
             if L % 2 == 0 and 2 ** (L // 2 + 1) <= 512 and 2 ** (L // 2 + 1) > 2 * nev:
                 assert m == 2 ** (L // 2 + 1)
+
+
+# ---------------------------------------------------------------- entanglement entropy (Eq. ee)
+
+def _bell_chain(L):
+    # Bell pairs (|00> + |11>)/sqrt 2 on qubits (0,1), (2,3), ...
+    bell = np.array([1, 0, 0, 1], dtype=np.complex128) / np.sqrt(2)  # index b0 + 2 b1
+    psi = np.array([1.0 + 0j])
+    for _ in range(L // 2):
+        psi = np.kron(bell, psi)  # new pair on the next two (higher) bits
+    return psi
+
+
+def test_entropy_pins():
+    from oracle import entropy
+    L = 8
+    # product state: zero for every cut
+    prod = np.array([1.0 + 0j])
+    rng = np.random.default_rng(3)
+    for _ in range(L):
+        q = rng.standard_normal(2) + 1j * rng.standard_normal(2)
+        prod = np.kron(q / np.linalg.norm(q), prod)
+    for LA in range(L + 1):
+        assert abs(entropy.entanglement_entropy(prod, L, LA)) < 1e-12
+    # Bell pairs on (0,1), (2,3), ...: ln 2 for a cut through one pair, 0 between pairs
+    bc = _bell_chain(L)
+    for LA in range(L + 1):
+        want = np.log(2) if LA % 2 == 1 else 0.0
+        assert abs(entropy.entanglement_entropy(bc, L, LA) - want) < 1e-12
+    # one Bell pair on qubits (0, 1), the other qubits in |0>: subsystem A is the LOW bits,
+    # so only the cut after qubit 0 is entangled
+    one = np.zeros(1 << L, dtype=np.complex128)
+    one[0] = one[3] = 1 / np.sqrt(2)
+    for LA in range(L + 1):
+        want = np.log(2) if LA == 1 else 0.0
+        assert abs(entropy.entanglement_entropy(one, L, LA) - want) < 1e-12
+    # GHZ: ln 2 for every proper cut
+    ghz = np.zeros(1 << L, dtype=np.complex128)
+    ghz[0] = ghz[-1] = 1 / np.sqrt(2)
+    for LA in range(1, L):
+        assert abs(entropy.entanglement_entropy(ghz, L, LA) - np.log(2)) < 1e-12
+    # maximally entangled across the middle cut: LA ln 2
+    LA = L // 2
+    mx = np.zeros(1 << L, dtype=np.complex128)
+    for a in range(1 << LA):
+        mx[a + (a << LA)] = 1
+    mx /= np.linalg.norm(mx)
+    assert abs(entropy.entanglement_entropy(mx, L, LA) - LA * np.log(2)) < 1e-12
+    # S_A = S_B for any pure state: the spectrum of rho_B = tr_A |psi><psi|, formed by an
+    # explicit partial trace, gives the same entropy as the singular values
+    x = inputs.complex_gaussian(1 << L, 4)
+    for LA in range(1, L):
+        M = np.array([[x[a + (b << LA)] for b in range(1 << (L - LA))] for a in range(1 << LA)])
+        rho_B = np.einsum("ab,ac->bc", M, M.conj())
+        lam = np.clip(np.linalg.eigvalsh(rho_B), 1e-300, None)
+        assert abs(entropy.entanglement_entropy(x, L, LA) + np.sum(lam * np.log(lam))) < 1e-12
+
+
+def test_page_value_pins():
+    from oracle import entropy
+    # two qubits: 1/4 + 1/3 - 1/4 = 1/3 nats, the known mean for random two-qubit states
+    assert abs(entropy.page_entropy(1, 1) - 1.0 / 3.0) < 1e-15
+    # large systems: ln m - m / (2 n) up to O(1/n)
+    for LA, LB in [(4, 12), (6, 10), (8, 8)]:
+        m, n = 2 ** LA, 2 ** LB
+        assert abs(entropy.page_entropy(LA, LB) - (np.log(m) - m / (2 * n))) < 2.0 / n
+    assert entropy.page_entropy(7, 3) == entropy.page_entropy(3, 7)
+    # random states average to the Page value
+    L, LA = 10, 4
+    s = [entropy.entanglement_entropy(inputs.complex_gaussian(1 << L, 100 + i), L, LA)
+         for i in range(40)]
+    assert abs(np.mean(s) - entropy.page_entropy(LA, L - LA)) < 4 * np.std(s) / np.sqrt(40) + 1e-3
+
+
+def test_entropy_of_product_eigenstates_J0():
+    # J = 0: U is a product of single-qubit unitaries, its (non-degenerate) eigenvectors are
+    # product states, so every cut has zero entanglement
+    from oracle import entropy
+    L = 6
+    op = model.KickedIsing(L, 0.0, 0.7, inputs.disorder(L, 1.0, 9))
+    w, V = np.linalg.eig(op.dense())
+    for j in range(0, 1 << L, 7):
+        v = V[:, j] / np.linalg.norm(V[:, j])
+        for LA in range(1, L):
+            assert entropy.entanglement_entropy(v, L, LA) < 1e-9
