@@ -186,6 +186,21 @@ int arnoldi_eigs_batched(int L, double J, double g, const double* h, int R,
  * otherwise FLOQUET_EINVAL. k and m are host pointers. */
 int floquet_suggest_params(int L, int nev, int max_m, int64_t* k, int* m);
 
+/* Entanglement entropy of states (Sec. 4, Eq. ee): for each state j and cut c, subsystem A =
+ * qubits 0 .. cuts[c] - 1 (the low bits of the amplitude index), B = the rest, and
+ *     S[j * ncut + c] = -sum_i lambda_i ln lambda_i
+ * over the eigenvalues lambda_i of the reduced density matrix of A (the squared singular
+ * values of the state as a 2^{L_A} x 2^{L - L_A} matrix). Computed on the GPU in float64:
+ * the Gram matrix of the smaller side, Householder tridiagonalisation, bisection. The paper's
+ * chain has open boundaries and one cut; this library's chain is periodic, so a block of
+ * L_A qubits has two boundaries, and the formula is the same.
+ * X: device, nvec states of d = 2^L complex128 (state j at X + j d), assumed normalised.
+ * cuts: host, ncut values in [0, L] (0 and L give 0). S: host, nvec * ncut doubles.
+ * Allocates device workspace (at most ~4 GiB per cut, processed in chunks of states).
+ * Synchronises `stream`. 1 <= L <= 24, 1 <= nvec <= 65535. */
+int entanglement_entropy(int L, const void* X, int nvec, const int* cuts, int ncut, double* S,
+                         void* stream);
+
 /* Measurement hook. While enabled (on != 0), every replay of a filter's k-step sweep graph is
  * bracketed by CUDA events on the stream it runs on, and the library accumulates the
  * elapsed device time, the number of U applications (vectors x steps) and their

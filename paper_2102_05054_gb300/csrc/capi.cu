@@ -489,3 +489,30 @@ extern "C" int floquet_suggest_params(int L, int nev, int max_m, int64_t* k, int
   *m = (int)mm;
   return FLOQUET_OK;
 }
+
+// ------------------------------------------------------------------ entanglement entropy (Sec. 4)
+
+namespace fq {
+int entanglement_entropy_run(int L, const double2* X, int nvec, const int* cuts, int ncut,
+                             double* S, cudaStream_t st);
+}
+
+extern "C" int entanglement_entropy(int L, const void* X, int nvec, const int* cuts, int ncut,
+                                    double* S, void* stream) {
+  if (L < 1 || L > 24 || !X || nvec < 1 || nvec > 65535 || !cuts || ncut < 1 || !S) {
+    set_error("entanglement_entropy: need 1 <= L <= 24, 1 <= nvec <= 65535, ncut >= 1 and "
+              "non-NULL pointers");
+    return FLOQUET_EINVAL;
+  }
+  for (int c = 0; c < ncut; ++c)
+    if (cuts[c] < 0 || cuts[c] > L) {
+      set_error("entanglement_entropy: cut %d = %d outside [0, L]", c, cuts[c]);
+      return FLOQUET_EINVAL;
+    }
+  if (!is_device_ptr(X)) {
+    set_error("entanglement_entropy: X must be device memory");
+    return FLOQUET_EINVAL;
+  }
+  return fq::entanglement_entropy_run(L, (const double2*)X, nvec, cuts, ncut, S,
+                                      (cudaStream_t)stream);
+}

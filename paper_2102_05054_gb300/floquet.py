@@ -48,6 +48,8 @@ SIGNATURES = {
     "floquet_profile_enable": (_c_int, [_c_int]),
     "floquet_profile_read": (_c_int, [_dptr, ctypes.POINTER(_c_int64), _dptr]),
     "floquet_launch_count": (_c_int64, []),
+    "entanglement_entropy": (_c_int, [_c_int, _c_void_p, _c_int, ctypes.POINTER(_c_int), _c_int,
+                                      _dptr, _c_void_p]),
     "floquet_suggest_params": (_c_int, [_c_int, _c_int, _c_int, ctypes.POINTER(_c_int64),
                                         ctypes.POINTER(_c_int)]),
     "floquet_reset_launch_count": (None, []),
@@ -273,3 +275,15 @@ def suggest_params(L, nev, max_m=512):
     _check(lib().floquet_suggest_params(int(L), int(nev), int(max_m), ctypes.byref(k),
                                         ctypes.byref(m)), "floquet_suggest_params")
     return int(k.value), int(m.value)
+
+
+def entanglement_entropy(L, X, cuts, stream=None):
+    """S[j, c] (numpy, nvec x ncut): entanglement entropy of state j of X (device complex128,
+    shape (nvec, 2^L) or (2^L,)) for subsystem A = the low cuts[c] qubits."""
+    cuts = np.ascontiguousarray(np.asarray(cuts, dtype=np.int32).ravel())
+    nvec = int(X.numel() // (1 << L))
+    S = np.zeros(nvec * len(cuts))
+    _check(lib().entanglement_entropy(int(L), _ptr(X), nvec,
+                                      cuts.ctypes.data_as(ctypes.POINTER(_c_int)), len(cuts),
+                                      _dp(S), _stream(stream)), "entanglement_entropy")
+    return S.reshape(nvec, len(cuts))
