@@ -197,7 +197,8 @@ int floquet_suggest_params(int L, int nev, int max_m, int64_t* k, int* m);
  * X: device, nvec states of d = 2^L complex128 (state j at X + j d), assumed normalised.
  * cuts: host, ncut values in [0, L] (0 and L give 0). S: host, nvec * ncut doubles.
  * Allocates device workspace (at most ~4 GiB per cut, processed in chunks of states).
- * Synchronises `stream`. 1 <= L <= 24, 1 <= nvec <= 65535. */
+ * Synchronises `stream`. 1 <= L <= 24, 1 <= nvec <= 65535, min(L_A, L - L_A) <= 11 (the
+ * Householder reduction runs in one CTA per matrix of side 2^min(L_A, L - L_A)). */
 int entanglement_entropy(int L, const void* X, int nvec, const int* cuts, int ncut, double* S,
                          void* stream);
 

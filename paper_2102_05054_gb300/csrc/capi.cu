@@ -504,11 +504,18 @@ extern "C" int entanglement_entropy(int L, const void* X, int nvec, const int* c
               "non-NULL pointers");
     return FLOQUET_EINVAL;
   }
-  for (int c = 0; c < ncut; ++c)
+  for (int c = 0; c < ncut; ++c) {
     if (cuts[c] < 0 || cuts[c] > L) {
       set_error("entanglement_entropy: cut %d = %d outside [0, L]", c, cuts[c]);
       return FLOQUET_EINVAL;
     }
+    // the Householder reduction runs in one CTA per matrix of side 2^min(L_A, L - L_A)
+    if (std::min(cuts[c], L - cuts[c]) > 11) {
+      set_error("entanglement_entropy: cut %d = %d needs a reduced density matrix of side "
+                "2^%d > 2048", c, cuts[c], std::min(cuts[c], L - cuts[c]));
+      return FLOQUET_EINVAL;
+    }
+  }
   if (!is_device_ptr(X)) {
     set_error("entanglement_entropy: X must be device memory");
     return FLOQUET_EINVAL;
