@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) gram_slab_kernel(const double2* __restric
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty in [0, 8)
   double2 acc[4];
   for (int q = 0; q < 4; ++q) acc[q] = make_double2(0, 0);
-  const int64_t i0 = (int64_t)s * slab, i1 = std::min<int64_t>(r, i0 + slab);
+  const int64_t i0 = (int64_t)s * slab, i1 = (i0 + slab < r) ? i0 + slab : r;
   for (int64_t ib = i0; ib < i1; ib += kGramTile) {
     // load 32 rows x 32 columns of both column tiles; the lane index runs along the
     // unit-stride direction so that the loads are coalesced

@@ -298,6 +298,7 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
   // converged values the Ritz vectors, Rayleigh quotients, residuals and the completeness
   // rule. Leaves nc[b] (converged prefix) and, in s.Y, the eigenvectors of H[:n, :n].
   std::vector<int> nc(B, 0);
+  bool near_done = false;  // set by check(): some unfinished problem has nev converged estimates
   auto check = [&](int n) -> int {
     FQ_TRY(small_eig_batched(s.H.p, s.ldh(), s.strideH(), n, B, s.lam.p, m, s.Y.p, m,
                              (int64_t)m * m, s.eigw.p, s.info.p, st));
@@ -324,6 +325,7 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
       }
       nc[b] = c;
       if (!res[b].done && c > nev) nx = std::max(nx, c);
+      if (!res[b].done && c >= nev) near_done = true;
     }
     if (nx > 0) {
       FQ_TRY(ks_ritz(s, n, nx, rq_h));
@@ -378,7 +380,10 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
     return FLOQUET_OK;
   };
 
-  const int check_every = 16;
+  // checks every 16 Krylov steps; for a few problems (a filter step then costs far more than
+  // a check), every 4 steps once some unfinished problem has nev converged Ritz estimates
+  // (only the completeness or residual test is left)
+  const int check_every = 16, check_every_near = B <= 4 ? 4 : 16;
   for (;; ++restarts) {
     // expand p -> m, checking for convergence every check_every steps once the basis can
     // hold nev + check_every Ritz pairs (the Krylov relation holds at every size)
@@ -392,8 +397,9 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
       const int n = j + 1;
       // (not for the FP32-filter form: its polish needs the full converged block as guard
       // directions, which only the complete Krylov space provides)
+      const int every = near_done ? check_every_near : check_every;
       if (precision != FLOQUET_FILTER_FP32 && n < m &&
-          n >= std::max(p + check_every, nev + check_every) && n % check_every == 0) {
+          n >= std::max(p + check_every, nev + check_every) && n % every == 0) {
         FQ_TRY(check(n));
         bool all = true;
         for (int b = 0; b < B; ++b) all &= res[b].done;
