@@ -3,11 +3,11 @@
  *
  * Method: D. J. Luitz, "Polynomial filter diagonalization of large Floquet unitary
  * operators", arXiv:2102.05054. The eigenpairs of a Floquet unitary U closest to a target
- * exp(i phi) on the unit circle are found by Arnoldi iteration (Sec. 3, Eq. arnoldi) on the
- * geometric-sum filter g_k(U) (Sec. 2, Eq. geo), followed by Rayleigh quotients
- * omega = <n|U|n> and residuals ||U|n> - omega|n>|| (Sec. 3, Eq. residual).
+ * exp(i phi) on the unit circle are found by Arnoldi iteration (Sec. 4, Eq. arnoldi) on the
+ * geometric-sum filter g_k(U) (Sec. 3, Eq. geo), followed by Rayleigh quotients
+ * omega = <n|U|n> and residuals ||U|n> - omega|n>|| (Sec. 4, Eq. residual).
  *
- * Operator (a local Floquet operator with a cheap matrix-free product, as Sec. 1 requires):
+ * Operator (a local Floquet operator with a cheap matrix-free product, as Sec. 2 requires):
  *   U = D K,  K = exp(-i g sum_i X_i),  D = exp(-i sum_i (J Z_i Z_{i+1} + h_i Z_i)),
  *   periodic chain of L qubits (bond (L-1, 0) included), 3 <= L <= 24.
  *   Amplitude index s = sum_i b_i 2^i (qubit i = bit i), Z|0> = +|0>.
@@ -66,7 +66,7 @@ enum floquet_dtype { FLOQUET_C128 = 0, FLOQUET_C64 = 1, FLOQUET_C128_DF = 2 };
  *   FLOQUET_FILTER_FP32 -- filter sweeps in complex64 with complex64 accumulation, FP64
  *                          Gram-Schmidt, Hessenberg/Schur, Ritz extraction and residuals,
  *                          then an FP64 Rayleigh-Ritz polish of the returned eigenpairs
- *                          (Sec. 3 footnote: one Ritz step with <n|U|m> on approximate
+ *                          (Sec. 4 footnote: one Ritz step with <n|U|m> on approximate
  *                          eigenvectors) iterated with defect-corrected filtering until the
  *                          U-residuals reach tol_resid. */
 /*   FLOQUET_FILTER_DF   -- filter sweeps in double-float (FLOQUET_C128_DF), FP64 for the
@@ -80,7 +80,7 @@ enum floquet_precision { FLOQUET_FP64 = 0, FLOQUET_FILTER_FP32 = 1, FLOQUET_FILT
  *                          per U application. */
 enum floquet_form { FLOQUET_FORM_ACC = 0, FLOQUET_FORM_HORNER = 1 };
 
-/* Create the operator U = D K (Sec. 1; model fixed above). h: host, L doubles, copied.
+/* Create the operator U = D K (Sec. 2; model fixed above). h: host, L doubles, copied.
  * Builds the diagonal-phase tables and the pass plan on the current device.
  * EINVAL if L outside [3, 24] or h/out NULL; ENOMEM/ECUDA on allocation failure. */
 int floquet_create(int L, double J, double g, const double* h, floquet_t* out);
@@ -91,20 +91,20 @@ int floquet_destroy(floquet_t op);
 /* d = 2^L. */
 int floquet_dim(floquet_t op, int64_t* d);
 
-/* psi_out[:, j] = U psi_in[:, j] for j < nvec (the matrix-free product of Sec. 1 that
- * Sec. 2 requires). psi_in, psi_out: device, nvec*d complex of `dtype`; may be equal
+/* psi_out[:, j] = U psi_in[:, j] for j < nvec (the matrix-free product of Sec. 2 that
+ * Sec. 3 requires). psi_in, psi_out: device, nvec*d complex of `dtype`; may be equal
  * (in place). Asynchronous on `stream`. */
 int floquet_apply_u(floquet_t op, const void* psi_in, void* psi_out, int nvec, int dtype,
                     void* stream);
 
-/* psi_out[:, j] = g_k(U) psi_in[:, j] (Sec. 2, Eq. geo, k terms) for j < nvec.
+/* psi_out[:, j] = g_k(U) psi_in[:, j] (Sec. 3, Eq. geo, k terms) for j < nvec.
  * psi_in, psi_out: device, nvec*d complex of `dtype`, must not overlap. k >= 1.
  * `form` selects the formulation (floquet_form). Asynchronous on `stream`; the k-step loop
  * runs as a captured CUDA graph that is cached in `op` for the same (k, nvec, dtype, form). */
 int filter_apply(floquet_t op, double phi, int64_t k, const void* psi_in, void* psi_out,
                  int nvec, int dtype, int form, void* stream);
 
-/* One classical Gram-Schmidt step with one full reorthogonalisation (CGS2) of Sec. 3's
+/* One classical Gram-Schmidt step with one full reorthogonalisation (CGS2) of Sec. 4's
  * Arnoldi process: w <- (w - V V^H w) / beta, twice projected, for n >= 0 orthonormal
  * columns V (device, d x n complex128, column-major, leading dimension d).
  * w: device, d complex128, overwritten with the unit vector. h: host, n+1 complex128
@@ -131,20 +131,20 @@ int gram_schmidt(int64_t d, const void* V, int n, void* w, double* h, void* stre
 int gram_schmidt_noalloc(int64_t d, const void* V, int n, void* w, void* h, void* stream);
 
 /* Eigen-decomposition of a small general complex matrix on the device (the Hessenberg /
- * Schur solve behind Sec. 3's Ritz pairs): A = Y diag(lambda) Y^{-1}.
+ * Schur solve behind Sec. 4's Ritz pairs): A = Y diag(lambda) Y^{-1}.
  * A: host or device, n x n complex128 column-major; lambda: host, n complex128; Y: host or
  * device, n x n complex128 column-major, unit-norm columns. 1 <= n <= 512. Order of the
  * eigenvalues: descending modulus. Synchronises `stream`. */
 int small_eig(int n, const void* A, double* lambda, void* Y, void* stream);
 
-/* Rayleigh quotients and residuals (Sec. 3, Eq. residual) of nvec vectors X (device, d x
+/* Rayleigh quotients and residuals (Sec. 4, Eq. residual) of nvec vectors X (device, d x
  * nvec complex128; normalised internally, X itself is not modified):
  * omega_j = <x_j|U|x_j>/<x_j|x_j>, resid_j = ||U x_j - omega_j x_j|| / ||x_j||.
  * omega: host, 2*nvec doubles; resid: host, nvec doubles. Synchronises `stream`. */
 int ritz_residuals(floquet_t op, const void* X, int nvec, double* omega, double* resid,
                    void* stream);
 
-/* The eigensolver of Secs. 2-3: Krylov-Schur restarted Arnoldi on g_k(U) with CGS2,
+/* The eigensolver of Secs. 3-4: Krylov-Schur restarted Arnoldi on g_k(U) with CGS2,
  * Krylov dimension m, keeping the nev eigenpairs of U whose eigenvalues are closest to
  * exp(i phi) by wrapped angle |arg(omega e^{-i phi})| (ties: ascending arg), eigenvalues as
  * Rayleigh quotients and residuals as in Eq. residual.
@@ -172,9 +172,10 @@ int arnoldi_eigs_batched(int L, double J, double g, const double* h, int R,
                          double tol_resid, int max_restarts, const void* v0, double* evals,
                          double* resid, int* n_conv, void* stream);
 
-/* The paper's choice of filter length and Krylov dimension (Sec. 3, strategy paragraph;
- * Sec. 4, parameter scan of Fig. bench): the runtime is minimal when the Krylov dimension is about 80 % of
- * the number of eigenvalues on the outer lobe of g_k (2d/k with k terms), and for large
+/* The paper's choice of filter length and Krylov dimension (Sec. 4, strategy paragraph;
+ * Sec. 5, parameter scan of Fig. bench): the runtime is minimal when the Krylov dimension is
+ * about 80 % of the number of eigenvalues on the outer lobe of g_k (2d/k with k terms), and
+ * for large
  * sizes the paper takes n_cv = floor(2^(L/2 + 1)) with k = 0.8 * 2^(L+1) / n_cv, and
  * n_cv > 2 nev. This library computes
  *     m = max(floor(2^(L/2 + 1)), 2 nev + 1), capped at min(max_m, d - 1),
@@ -186,7 +187,7 @@ int arnoldi_eigs_batched(int L, double J, double g, const double* h, int R,
  * otherwise FLOQUET_EINVAL. k and m are host pointers. */
 int floquet_suggest_params(int L, int nev, int max_m, int64_t* k, int* m);
 
-/* Entanglement entropy of states (Sec. 4, Eq. ee): for each state j and cut c, subsystem A =
+/* Entanglement entropy of states (Sec. 5, Eq. ee): for each state j and cut c, subsystem A =
  * qubits 0 .. cuts[c] - 1 (the low bits of the amplitude index), B = the rest, and
  *     S[j * ncut + c] = -sum_i lambda_i ln lambda_i
  * over the eigenvalues lambda_i of the reduced density matrix of A (the squared singular

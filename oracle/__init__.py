@@ -4,7 +4,7 @@ This package is TEST INFRASTRUCTURE. It is a plain, slow, complex128 numpy/scipy
 restatement of what the GPU path computes, written from the paper:
 
 * ``oracle.model``  -- the kicked-Ising Floquet operator U = D.K applied matrix-free
-  (Sec. 1: local Floquet operators admit a cheap matrix-free product), its dense form by
+  (Sec. 2: local Floquet operators admit a cheap matrix-free product), its dense form by
   Kronecker products and matrix exponentials, and the special cases whose spectra
   are known in closed form.
 * ``oracle.geosum`` -- the geometric sum g_k(U) (Eq. geo, k-term reading), in the
@@ -13,7 +13,7 @@ restatement of what the GPU path computes, written from the paper:
 * ``oracle.krylov`` -- Arnoldi with classical Gram-Schmidt and one
   reorthogonalisation (Eq. arnoldi), Rayleigh quotients and residuals (Eq. residual),
   the selection of the eigenpairs closest to the target, dense diagonalisation and
-  ARPACK on g_k(U) (Sec. 3).
+  ARPACK on g_k(U) (Sec. 4).
 
 It shares no code with the CUDA path and neither imports the other. Only ``tests/``,
 ``__graft_entry__.smoke()`` and ``bench.py`` (its CPU-baseline leg and its

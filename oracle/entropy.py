@@ -1,7 +1,7 @@
 """Entanglement entropy of eigenstates and the Page value, CPU oracle (test infrastructure:
 only tests/, __graft_entry__.smoke() and bench.py's CPU arms use it).
 
-Sec. 4 of Luitz, arXiv:2102.05054 (Eq. ee): cut the chain into subsystem A of L_A qubits and
+Sec. 5 of Luitz, arXiv:2102.05054 (Eq. ee): cut the chain into subsystem A of L_A qubits and
 B of L - L_A qubits, S_A = -sum_i s_i^2 ln s_i^2 with s_i the singular values of the state
 reshaped as a 2^{L_A} x 2^{L - L_A} matrix (rows indexed by A). Subsystem A is qubits
 0 .. L_A - 1 here, i.e. the low L_A bits of the amplitude index (qubit i = bit i), so the

@@ -1,6 +1,6 @@
 """Geometric-sum polynomial filter g_k(U), CPU oracle (test infrastructure).
 
-Sec. 2, Eq. geo defines the filter as a geometric series in exp(-i phi_tgt) U. This
+Sec. 3, Eq. geo defines the filter as a geometric series in exp(-i phi_tgt) U. This
 project counts k as the NUMBER OF TERMS:
 
     g_k(U) = sum_{j=0}^{k-1} z^j U^j,    z = exp(-i phi),

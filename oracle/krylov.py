@@ -1,12 +1,12 @@
 """Arnoldi on g_k(U), Rayleigh quotients, residuals and target selection: CPU oracle
 (test infrastructure; see ``oracle/__init__``).
 
-Sec. 3 builds an orthonormal Krylov basis V of g_k(U) from a random start vector,
+Sec. 4 builds an orthonormal Krylov basis V of g_k(U) from a random start vector,
 projects g_k(U) to the upper Hessenberg H_m = V^H g_k(U) V (Eq. arnoldi), takes Ritz pairs
 of H_m, and then recovers the eigenvalue of U from the Ritz vector |n> by the Rayleigh
 quotient omega_n = <n|U|n> together with the residual r_n = ||U|n> - omega_n |n>||_2
 (Eq. residual). The paper runs ARPACK's implicitly restarted Arnoldi; ``arpack_eigs`` does
-the same through scipy. The plain definition of the result (Sec. 2: all nev eigenpairs of
+the same through scipy. The plain definition of the result (Sec. 3: all nev eigenpairs of
 U with eigenvalues nearest the target on the unit circle) is ``dense_eigs``.
 
 Readings taken where the paper is silent:
@@ -94,7 +94,7 @@ def dense_eigs(op, phi, nev):
 
 
 def arpack_eigs(op, phi, k, nev, m, v0, tol=1e-13, max_req=None):
-    """Sec. 3 route: ARPACK ('LM') on g_k(U), then omega = <n|U|n> and r_n.
+    """Sec. 4 route: ARPACK ('LM') on g_k(U), then omega = <n|U|n> and r_n.
 
     ARPACK ranks Ritz values by |g_k|, which orders eigenvalues by closeness only inside
     the main lobe |x| < 2 pi / k. The number of requested pairs n_req is therefore grown
@@ -129,9 +129,9 @@ def arpack_eigs(op, phi, k, nev, m, v0, tol=1e-13, max_req=None):
 def paper_params(L, nev, max_m=512):
     """Filter length k (number of terms) and Krylov dimension m by the paper's rule.
 
-    Sec. 3 (strategy paragraph) takes the Krylov dimension near the number of eigenvalues on
+    Sec. 4 (strategy paragraph) takes the Krylov dimension near the number of eigenvalues on
     the outer lobe of g_k, 2d/(number of terms), and larger than twice the number of wanted
-    pairs; Sec. 4 (scan of Fig. bench) finds the fastest runs at 80 % of that count and then
+    pairs; Sec. 5 (scan of Fig. bench) finds the fastest runs at 80 % of that count and then
     fixes n_cv = floor(2^(L/2+1)) and k = 0.8 * 2^(L+1) / n_cv for large sizes. The paper
     gives no rounding for k: it is rounded to the nearest integer here (the quotient
     2^(L+3)/(5 n_cv) is never a tie). A cap on m (the GPU's small eigensolver takes m <= 512)

@@ -1,8 +1,8 @@
 """Kicked-Ising Floquet operator, CPU oracle (test infrastructure; see ``oracle/__init__``).
 
-The paper (Sec. 1, Eqs. U/unitary) benchmarks a brickwork circuit; its method applies to
+The paper (Sec. 2, Eqs. U/unitary) benchmarks a brickwork circuit; its method applies to
 any local Floquet operator with a cheap matrix-free product (Sec. 1, the overview of the
-method and the paragraph after Eq. matvec).
+method; Sec. 2, the paragraph after Eq. matvec).
 The operator here is the periodically kicked Ising chain
 
     U = D . K,   K = exp(-i g sum_i X_i),   D = exp(-i sum_i (J Z_i Z_{i+1} + h_i Z_i)),

@@ -461,7 +461,7 @@ const char* floquet_last_error(void) { return get_error(); }
 
 }  // extern "C"
 
-// ------------------------------------------------------------------ parameter rule (Secs. 3-4)
+// ------------------------------------------------------------------ parameter rule (Secs. 4-5)
 
 extern "C" int floquet_suggest_params(int L, int nev, int max_m, int64_t* k, int* m) {
   if (L < 3 || L > 24 || nev < 1 || !k || !m) {
@@ -490,7 +490,7 @@ extern "C" int floquet_suggest_params(int L, int nev, int max_m, int64_t* k, int
   return FLOQUET_OK;
 }
 
-// ------------------------------------------------------------------ entanglement entropy (Sec. 4)
+// ------------------------------------------------------------------ entanglement entropy (Sec. 5)
 
 namespace fq {
 int entanglement_entropy_run(int L, const double2* X, int nvec, const int* cuts, int ncut,

@@ -1,4 +1,4 @@
-// Entanglement entropy of eigenstates (Luitz, arXiv:2102.05054, Sec. 4, Eq. ee): cut the chain
+// Entanglement entropy of eigenstates (Luitz, arXiv:2102.05054, Sec. 5, Eq. ee): cut the chain
 // into A = qubits 0 .. L_A - 1 (the low bits of the amplitude index) and B = the rest;
 // S_A = -sum_i lambda_i ln lambda_i over the eigenvalues of the reduced density matrix, which
 // are the squared singular values of the state as a 2^{L_A} x 2^{L - L_A} matrix

@@ -1,6 +1,6 @@
 // Internal declarations shared by the CUDA translation units of libfloquet.
 //
-// Model (Sec. 1 of Luitz, arXiv:2102.05054, with the kicked-Ising operator of this library):
+// Model (Sec. 2 of Luitz, arXiv:2102.05054, with the kicked-Ising operator of this library):
 //   U = D K, K = prod_q exp(-i g X_q), D_s = exp(-i theta_s),
 //   theta_s = J sum_i z_i z_{i+1 mod L} + sum_i h_i z_i, z_i = 1 - 2 b_i(s).
 #pragma once

@@ -1,4 +1,4 @@
-// Krylov-basis linear algebra in complex128 (Sec. 3 of Luitz, arXiv:2102.05054: the
+// Krylov-basis linear algebra in complex128 (Sec. 4 of Luitz, arXiv:2102.05054: the
 // Arnoldi process with Gram-Schmidt orthogonalisation, Ritz vectors V y, Rayleigh quotients
 // and residuals of Eq. residual).
 //

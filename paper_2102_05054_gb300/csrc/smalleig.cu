@@ -1,5 +1,5 @@
 // Small dense complex eigensolver on the device: the Ritz pairs of the projected matrix
-// H_m = V^H g_k(U) V of Sec. 3 (Eq. arnoldi) of Luitz, arXiv:2102.05054, where the paper
+// H_m = V^H g_k(U) V of Sec. 4 (Eq. arnoldi) of Luitz, arXiv:2102.05054, where the paper
 // relies on ARPACK's dense routines. One CTA per matrix, matrices in global memory (they are
 // small and stay in L1/L2):
 //   1. Householder reduction to upper Hessenberg form, Q accumulated;

@@ -1,4 +1,4 @@
-// Krylov-Schur restarted Arnoldi on the geometric-sum filter g_k(U) (Secs. 2-3 of Luitz,
+// Krylov-Schur restarted Arnoldi on the geometric-sum filter g_k(U) (Secs. 3-4 of Luitz,
 // arXiv:2102.05054), batched over independent problems that advance in lockstep.
 //
 // Per restart cycle and problem b:
@@ -522,7 +522,7 @@ static int orthonormalize(Workspace& ws, double2* X, int n, int64_t d, double dr
   return FLOQUET_OK;
 }
 
-// FP64 polish of the FILTER_FP32 result (Sec. 3 footnote: a Ritz step with U on approximate
+// FP64 polish of the FILTER_FP32 result (Sec. 4 footnote: a Ritz step with U on approximate
 // eigenvectors, here iterated). Each iteration: Rayleigh-Ritz with U on span(S); keep the nb
 // Ritz pairs with the largest |g_k(omega)| (the block the filter enhances); stop when the nev
 // closest in-lobe pairs have residuals <= tol_resid; otherwise extend S by the

@@ -1,5 +1,5 @@
 // Matrix-free application of the kicked-Ising Floquet operator U = D K and of the
-// geometric-sum filter g_k(U) (Luitz, arXiv:2102.05054: Sec. 1 matrix-free product, Sec. 2
+// geometric-sum filter g_k(U) (Luitz, arXiv:2102.05054: Sec. 2 matrix-free product, Sec. 3
 // Eq. geo).
 //
 // Kick layer. exp(-i g X_q) = c I - i s X_q acts on the amplitude pair (s, s xor 2^q).

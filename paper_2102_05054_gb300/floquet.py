@@ -268,7 +268,7 @@ def reset_launch_count():
 
 
 def suggest_params(L, nev, max_m=512):
-    """(k, m) by the paper's rule (Secs. 3-4): m = max(floor(2^(L/2+1)), 2 nev + 1) capped at
+    """(k, m) by the paper's rule (Secs. 4-5): m = max(floor(2^(L/2+1)), 2 nev + 1) capped at
     min(max_m, d - 1), k = round(0.8 * 2^(L+1) / m). Host only."""
     k = _c_int64(0)
     m = _c_int(0)

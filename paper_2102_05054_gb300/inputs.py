@@ -7,7 +7,7 @@ workloads. Both the oracle and the GPU path receive these values as plain arrays
 Disorder: h_i ~ U[-W, W] from ``numpy.random.default_rng(seed).uniform`` (the paper draws
 its random circuits from a seeded generator; it names none, so numpy's PCG64 is used).
 Start vector: complex Gaussian (independent real and imaginary parts), normalised
-(Sec. 3 starts Arnoldi from a random vector).
+(Sec. 4 starts Arnoldi from a random vector).
 """
 
 import math

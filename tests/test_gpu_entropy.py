@@ -1,4 +1,4 @@
-"""GPU entanglement entropy (Sec. 4, Eq. ee) against the CPU oracle, through the C ABI.
+"""GPU entanglement entropy (Sec. 5, Eq. ee) against the CPU oracle, through the C ABI.
 
 Bar: |S_gpu - S_oracle| <= 1e-10 (float64 throughout; the Gram matrix squares the singular
 values, so eigenvalues near 0 lose relative accuracy, but they contribute -lambda ln lambda

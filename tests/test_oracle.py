@@ -161,7 +161,7 @@ def test_gk_paper_facts(k):
 
 
 def test_lobe_count_statistics():
-    # 2d/k eigenvalues on the outer lobe on average (Sec. 2); across targets the mean count
+    # 2d/k eigenvalues on the outer lobe on average (Sec. 3); across targets the mean count
     # over 16 targets must be close to 2d/k.
     L, k = 10, 32
     op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 11))
@@ -183,7 +183,7 @@ def test_filter_closed_form_on_exact_eigenvectors():
 
 
 def test_filter_peaks_at_target_eigenvalue():
-    # Sec. 2: the phase factor rotates the target to 1, where |g_k| peaks at the number of
+    # Sec. 3: the phase factor rotates the target to 1, where |g_k| peaks at the number of
     # terms. Choose phi = arg(omega) for an exact eigenvalue: g_k(U) v = k v.
     L, k = 7, 23
     op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 23))
@@ -352,7 +352,7 @@ def test_planted_single_gram_schmidt_pass_is_caught(monkeypatch):
 
 
 def test_paper_params_pins():
-    # Sec. 4 fixes n_cv = floor(2^(L/2+1)) and k = 0.8 * 2^(L+1) / n_cv; for even L the
+    # Sec. 5 fixes n_cv = floor(2^(L/2+1)) and k = 0.8 * 2^(L+1) / n_cv; for even L the
     # Krylov dimension is a power of two, and in every case the Krylov dimension is about
     # 80 % of the outer-lobe count 2d/k and more than twice the number of wanted pairs
     assert krylov.paper_params(12, 50) == (51, 128)    # 0.8 * 8192 / 128 = 51.2
