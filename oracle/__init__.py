@@ -15,6 +15,11 @@ restatement of what the GPU path computes, written from the paper:
   the selection of the eigenpairs closest to the target, dense diagonalisation and
   ARPACK on g_k(U) (Sec. 4).
 
+* ``oracle.brickwork`` -- the paper's own two-layer brickwork circuit of two-qubit gates
+  (Sec. 2, Eqs. U, unitary), applied gate by gate.
+* ``oracle.entropy`` -- entanglement entropy of a state for a cut of the chain and the
+  Page value for random states (Sec. 5, Eqs. ee, page).
+
 It shares no code with the CUDA path and neither imports the other. Only ``tests/``,
 ``__graft_entry__.smoke()`` and ``bench.py`` (its CPU-baseline leg and its
 ``--impl reference`` arm) may import it; the product path never calls it.
@@ -26,4 +31,4 @@ closed-form special cases, the paper's statements about g_k, brute force on tiny
 inputs).
 """
 
-from . import model, geosum, krylov  # noqa: F401
+from . import brickwork, entropy, geosum, krylov, model  # noqa: F401

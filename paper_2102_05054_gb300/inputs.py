@@ -36,6 +36,26 @@ def start_vector(L, seed=START_SEED):
     return complex_gaussian(1 << L, seed)
 
 
+def haar_unitary(n, rng):
+    """n x n unitary from the uniform (Haar) measure: QR of a complex Gaussian matrix with
+    the phases of R's diagonal moved into Q (the sampling the paper cites for its gates)."""
+    z = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    dg = np.diag(r)
+    return (q * (dg / np.abs(dg))).astype(np.complex128)
+
+
+def brickwork_gates(L, seed):
+    """Random gates of the two-layer brickwork circuit on L qubits (L even): bond gates
+    g2[i] (4 x 4, acting on qubits i and i+1, i = 0..L-2) and the two boundary gates g1[0]
+    on qubit 0 and g1[1] on qubit L-1 (2 x 2). Matrix indices of a bond gate are
+    b_i + 2 b_{i+1} (row = output, column = input)."""
+    rng = np.random.default_rng(seed)
+    g2 = np.stack([haar_unitary(4, rng) for _ in range(L - 1)])
+    g1 = np.stack([haar_unitary(2, rng) for _ in range(2)])
+    return g2, g1
+
+
 def random_states(d, n, seed):
     """n independent normalised complex Gaussian states as a d x n column-major block."""
     return np.stack([complex_gaussian(d, seed + i) for i in range(n)], axis=1)

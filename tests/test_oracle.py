@@ -456,3 +456,82 @@ def test_entropy_of_product_eigenstates_J0():
         v = V[:, j] / np.linalg.norm(V[:, j])
         for LA in range(1, L):
             assert entropy.entanglement_entropy(v, L, LA) < 1e-9
+
+
+# ---------------------------------------------------------------- brickwork circuit (Sec. 2)
+
+def _brick(L, g2=None, g1=None, seed=5):
+    from oracle import brickwork
+    r2, r1 = inputs.brickwork_gates(L, seed)
+    return brickwork.Brickwork(L, r2 if g2 is None else g2, r1 if g1 is None else g1)
+
+
+def test_brickwork_unitary_and_dense():
+    op = _brick(6)
+    U = op.dense()
+    assert np.abs(U.conj().T @ U - np.eye(64)).max() < 1e-13
+    # Haar gates give a dense U in the computational basis (Sec. 2)
+    assert np.mean(np.abs(U) > 1e-12) == 1.0
+    x = inputs.complex_gaussian(64, 3)
+    assert np.allclose(U @ x, op.apply_u(x), atol=1e-14)
+
+
+def test_brickwork_gate_index_convention():
+    # bond gates I (x) X act on the LOW qubit of each bond (index b_i + 2 b_{i+1}); the
+    # boundary gates are identities: U_b flips qubits 1, 3, .., L-3 and U_a flips 0, 2, ..,
+    # L-2, so U |s> = |s xor (2^(L-1) - 1)>
+    L = 6
+    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    g2 = np.stack([np.kron(np.eye(2), X)] * (L - 1))
+    g1 = np.stack([np.eye(2, dtype=np.complex128)] * 2)
+    op = _brick(L, g2, g1)
+    for s in range(1 << L):
+        e = np.zeros(1 << L, dtype=np.complex128)
+        e[s] = 1
+        y = op.apply_u(e)
+        assert abs(y[s ^ ((1 << (L - 1)) - 1)] - 1) < 1e-15 and np.abs(y).sum() - 1 < 1e-14
+
+
+def test_brickwork_layer_order():
+    # U = U_a U_b: U_b acts first. With X on qubit 0 in U_b and a CNOT (control qubit 0,
+    # target qubit 1) on bond (0,1) in U_a, |00..0> goes to |..011> (index 3); the other
+    # order would give index 1
+    L = 4
+    I4 = np.eye(4, dtype=np.complex128)
+    cnot = I4[:, [0, 3, 2, 1]]  # column b0 + 2 b1 -> row b0 + 2 (b1 xor b0)
+    g2 = np.stack([cnot, I4, I4])
+    g1 = np.stack([np.array([[0, 1], [1, 0]], dtype=np.complex128), np.eye(2)])
+    op = _brick(L, g2, g1)
+    e = np.zeros(16, dtype=np.complex128)
+    e[0] = 1
+    y = op.apply_u(e)
+    assert abs(y[3] - 1) < 1e-15
+
+
+def test_brickwork_product_gates_spectrum():
+    # bond gates that are products of single-qubit unitaries make U a product over qubits:
+    # its eigenvalues are the products of the per-qubit 2 x 2 eigenvalues (closed form)
+    L = 6
+    rng = np.random.default_rng(11)
+    A = [inputs.haar_unitary(2, rng) for _ in range(L - 1)]  # low factor of bond i
+    B = [inputs.haar_unitary(2, rng) for _ in range(L - 1)]  # high factor of bond i
+    g2 = np.stack([np.kron(B[i], A[i]) for i in range(L - 1)])
+    g1 = np.stack([inputs.haar_unitary(2, rng) for _ in range(2)])
+    op = _brick(L, g2, g1)
+    per_qubit = []
+    for q in range(L):
+        # factor from U_b (first), then from U_a
+        if q == 0:
+            fb = g1[0]
+        elif q == L - 1:
+            fb = g1[1]
+        else:
+            fb = A[q] if q % 2 == 1 else B[q - 1]
+        fa = A[q] if q % 2 == 0 else B[q - 1]
+        per_qubit.append(np.linalg.eigvals(fa @ fb))
+    lam = np.array([1.0 + 0j])
+    for ev in per_qubit:
+        lam = np.outer(ev, lam).ravel()
+    got = np.linalg.eigvals(op.dense())
+    for x in lam:
+        assert np.min(np.abs(got - x)) < 1e-12
