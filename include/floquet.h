@@ -80,6 +80,23 @@ enum floquet_precision { FLOQUET_FP64 = 0, FLOQUET_FILTER_FP32 = 1, FLOQUET_FILT
  *                          per U application. */
 enum floquet_form { FLOQUET_FORM_ACC = 0, FLOQUET_FORM_HORNER = 1 };
 
+/* Create the paper's own Floquet operator instead (Sec. 2, Eqs. U, unitary): a two-layer
+ * brickwork circuit on L qubits (L even, 4 <= L <= 24), U = U_a U_b with
+ *     U_b = u_0 u_{1,2} u_{3,4} ... u_{L-3,L-2} u_{L-1}   (acts first),
+ *     U_a = u_{0,1} u_{2,3} ... u_{L-2,L-1},
+ * qubit i = bit i of the amplitude index. g2: host, (L-1) bond gates u_{i,i+1}, each a
+ * row-major 4 x 4 complex matrix (interleaved re, im: element (r, c) of bond i at doubles
+ * 32 i + 2 (4 r + c)) whose indices are b_i + 2 b_{i+1}; g1: host, u_0 then u_{L-1}, row-major
+ * 2 x 2 complex (16 doubles). Gates are copied and are expected to be unitary (the paper
+ * draws them from the Haar measure). The matrix-free product is the paper's Eq. matvec: U is
+ * split at an odd qubit q into U_L (qubits 0..q) and U_R (qubits q..L-1), U = (U_L x 1)
+ * (1 x U_R), both built here as dense float64 matrices of side 2^(q+1) and 2^(L-q), and
+ * every U application is two complex GEMMs (cuBLAS ZGEMM) on two reshapes of the state.
+ * The returned handle works with floquet_apply_u, filter_apply, ritz_residuals and
+ * arnoldi_eigs in complex128 / FLOQUET_FP64 only (other dtypes and precisions:
+ * FLOQUET_EINVAL). Allocates U_L, U_R and a 32 MiB cuBLAS workspace on the current device. */
+int brickwork_create(int L, const double* g2, const double* g1, floquet_t* out);
+
 /* Create the operator U = D K (Sec. 2; model fixed above). h: host, L doubles, copied.
  * Builds the diagonal-phase tables and the pass plan on the current device.
  * EINVAL if L outside [3, 24] or h/out NULL; ENOMEM/ECUDA on allocation failure. */

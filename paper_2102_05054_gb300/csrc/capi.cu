@@ -236,6 +236,39 @@ int floquet_create(int L, double J, double g, const double* h, floquet_t* out) {
   FQ_GUARD_END
 }
 
+int brickwork_create(int L, const double* g2, const double* g1, floquet_t* out) {
+  FQ_GUARD_BEGIN
+  if (!out || !g2 || !g1) {
+    set_error("brickwork_create: NULL argument");
+    return FLOQUET_EINVAL;
+  }
+  *out = nullptr;
+  if (L < 4 || L > 24 || (L & 1)) {
+    set_error("brickwork_create: L = %d must be even and in [4, 24]", L);
+    return FLOQUET_EINVAL;
+  }
+  for (int i = 0; i < 32 * (L - 1); ++i)
+    if (!std::isfinite(g2[i])) {
+      set_error("brickwork_create: g2[%d] is not finite", i);
+      return FLOQUET_EINVAL;
+    }
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(g1[i])) {
+      set_error("brickwork_create: g1[%d] is not finite", i);
+      return FLOQUET_EINVAL;
+    }
+  floquet_op* op = new floquet_op();
+  const int rc = brick_init(op, L, g2, g1);
+  if (rc != FLOQUET_OK) {
+    op_free(op);
+    delete op;
+    return rc;
+  }
+  *out = op;
+  return clear_and(FLOQUET_OK);
+  FQ_GUARD_END
+}
+
 int floquet_destroy(floquet_t op) {
   if (!op) return FLOQUET_OK;
   op_free(op);

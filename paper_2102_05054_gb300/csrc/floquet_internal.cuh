@@ -225,9 +225,25 @@ struct Plan {
   std::vector<Pass> passes;  // first pass kicks [0, NB); the last applies the epilogue
 };
 
+// The brickwork random-circuit operator (brickwork.cu): U = (U_L x 1)(1 x U_R) split at the
+// odd qubit q, applied as two complex GEMMs (cuBLAS), complex128 only.
+struct BrickOp {
+  int L = 0, q = 0;
+  int64_t dL = 0, dR = 0;          // 2^(q+1), 2^(L-q)
+  double2* UL = nullptr;           // dL x dL, column-major
+  double2* UR = nullptr;           // dR x dR, column-major
+  double2* tmp = nullptr;          // GEMM intermediate, nvec x d
+  size_t tmp_elems = 0;
+  double2* consts = nullptr;       // device (1, 0) for the device-pointer GEMMs
+  void* cublas = nullptr;          // cublasHandle_t
+  void* ws = nullptr;              // cuBLAS workspace (fixed, so no GEMM allocates)
+  size_t ws_bytes = 0;
+};
+
 }  // namespace fq
 
 struct floquet_op {
+  fq::BrickOp* brick = nullptr;  // non-null: the brickwork operator instead of kicked Ising
   int L;
   double J, g;
   std::vector<double> h;  // L (or R*L for a batch)
@@ -263,6 +279,17 @@ namespace fq {
 // Builds tables and plans for `nprob` problems (h: nprob * L doubles).
 int op_init(floquet_op* op, int L, double J, double g, const double* h, int nprob);
 void op_free(floquet_op* op);
+
+// Brickwork operator (brickwork.cu). g2: (L-1) row-major 4 x 4 complex bond gates, g1: two
+// row-major 2 x 2 boundary gates, interleaved (re, im) doubles.
+int brick_init(floquet_op* op, int L, const double* g2, const double* g1);
+void brick_free(BrickOp* b);
+int brick_reserve(BrickOp* b, int nvec);
+int brick_apply(BrickOp* b, const double2* in, double2* out, int nvec, cudaStream_t st);
+int brick_horner_step(BrickOp* b, double2* acc, const double2* psi_in, const double2* zs,
+                      int nvec, cudaStream_t st);
+int brick_acc_step(BrickOp* b, double2* work, double2* acc, const double2* coef,
+                   int64_t coef_stride, int j, int nvec, cudaStream_t st);
 
 // U application on nvec vectors (vector v belongs to problem v / vec_per_prob).
 template <typename Real>

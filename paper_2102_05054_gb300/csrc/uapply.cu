@@ -386,6 +386,8 @@ static void destroy_graphs(floquet_op* op) {
 
 void op_free(floquet_op* op) {
   destroy_graphs(op);
+  brick_free(op->brick);
+  op->brick = nullptr;
   if (op->cap_stream) cudaStreamDestroy(op->cap_stream);
   if (op->ev_in) cudaEventDestroy(op->ev_in);
   if (op->ev_out) cudaEventDestroy(op->ev_out);
@@ -512,6 +514,14 @@ template <typename Real> static int tune(floquet_op* op, int nvec, cudaStream_t 
 template <typename Real>
 int apply_u(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int nvec, int vec_per_prob,
             cudaStream_t st) {
+  if (op->brick) {
+    if constexpr (std::is_same<Real, double>::value) {
+      return brick_apply(op->brick, in, out, nvec, st);
+    } else {
+      set_error("brickwork operator: complex128 sweeps only");
+      return FLOQUET_EINVAL;
+    }
+  }
   FQ_TRY(tune<Real>(op, nvec, st));
   return u_passes<Real>(op, in, out, nvec, vec_per_prob, EPI_PHASE, nullptr, nullptr, 0, 0,
                         nullptr, st);
@@ -624,16 +634,28 @@ int filter_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio
                 int vec_per_prob, bool use_graph, cudaStream_t st) {
   using C = cplx<Real>;
   const int64_t d = op->d;
-  FQ_TRY(tune<Real>(op, nvec, st));
+  if (op->brick && !std::is_same<Real, double>::value) {
+    set_error("brickwork operator: complex128 sweeps only");
+    return FLOQUET_EINVAL;
+  }
+  if (!op->brick) FQ_TRY(tune<Real>(op, nvec, st));
   FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
   C* work = reinterpret_cast<C*>(op->work);
   C* acc = reinterpret_cast<C*>(op->acc);
+  if (op->brick) FQ_TRY(brick_reserve(op->brick, nvec));  // before any capture
   FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, work, acc, coef, k, d, nvec, st)));
-  const int np = (int)plan_of<Real>(op).passes.size();
+  const int np = op->brick ? 2 + nvec : (int)plan_of<Real>(op).passes.size();
   auto body = [&](cudaStream_t s) -> int {
-    for (int64_t j = 1; j < k; ++j)
+    for (int64_t j = 1; j < k; ++j) {
+      if constexpr (std::is_same<Real, double>::value) {
+        if (op->brick) {
+          FQ_TRY(brick_acc_step(op->brick, work, acc, coef, k, (int)j, nvec, s));
+          continue;
+        }
+      }
       FQ_TRY(u_passes<Real>(op, work, work, nvec, vec_per_prob, EPI_PHASE_ACC, acc, coef, k,
                             (int)j, nullptr, s));
+    }
     return FLOQUET_OK;
   };
   if (k > 1)
@@ -660,6 +682,28 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
                   int vec_per_prob, bool use_graph, cudaStream_t st) {
   using C = cplx<Real>;
   const int64_t d = op->d;
+  if (op->brick) {
+    if constexpr (std::is_same<Real, double>::value) {
+      // brickwork: acc = psi_in + z U acc with U as two GEMMs, z as the second GEMM's alpha
+      FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
+      FQ_TRY(brick_reserve(op->brick, nvec));  // before any capture
+      C* bpin = reinterpret_cast<C*>(op->psi_in_copy);
+      C* bacc = reinterpret_cast<C*>(op->acc);
+      FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, bpin, bacc, nullptr, 0, d, nvec, st)));
+      auto bbody = [&](cudaStream_t s) -> int {
+        for (int64_t j = 1; j < k; ++j)
+          FQ_TRY(brick_horner_step(op->brick, bacc, bpin, zs, nvec, s));
+        return FLOQUET_OK;
+      };
+      if (k > 1)
+        FQ_TRY(run_loop(op, use_graph, k, nvec, sweep_dtype<Real>(), FLOQUET_FORM_HORNER, zs,
+                        vec_per_prob, (k - 1) * (1 + nvec), st, bbody));
+      return launch_convert_strided<Real, Rio>(bacc, out, out_stride, d, nvec, st);
+    } else {
+      set_error("brickwork operator: complex128 sweeps only");
+      return FLOQUET_EINVAL;
+    }
+  }
   FQ_TRY(tune<Real>(op, nvec, st));
   FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
   C* pin = reinterpret_cast<C*>(op->psi_in_copy);

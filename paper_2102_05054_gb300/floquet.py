@@ -30,6 +30,7 @@ _iptr = ctypes.POINTER(ctypes.c_int)
 SIGNATURES = {
     "floquet_create": (_c_int, [_c_int, _c_double, _c_double, _dptr, ctypes.POINTER(_c_void_p)]),
     "floquet_destroy": (_c_int, [_c_void_p]),
+    "brickwork_create": (_c_int, [_c_int, _dptr, _dptr, ctypes.POINTER(_c_void_p)]),
     "floquet_dim": (_c_int, [_c_void_p, ctypes.POINTER(_c_int64)]),
     "floquet_apply_u": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_int, _c_void_p]),
     "filter_apply": (_c_int, [_c_void_p, _c_double, _c_int64, _c_void_p, _c_void_p, _c_int,
@@ -141,6 +142,27 @@ class Floquet:
         d = ctypes.c_int64()
         _check(lib().floquet_dim(self.handle, ctypes.byref(d)), "floquet_dim")
         self.d = d.value
+
+    @classmethod
+    def brickwork(cls, L, g2, g1):
+        """The paper's brickwork random circuit (brickwork_create): g2 ((L-1) x 4 x 4) bond
+        gates with indices b_i + 2 b_{i+1}, g1 (2 x 2 x 2) boundary gates on qubits 0 and
+        L-1; complex128 sweeps and the FP64 eigensolver only."""
+        g2 = np.ascontiguousarray(g2, dtype=np.complex128)
+        g1 = np.ascontiguousarray(g1, dtype=np.complex128)
+        if g2.shape != (L - 1, 4, 4) or g1.shape != (2, 2, 2):
+            raise ValueError("g2 must be (L-1) x 4 x 4 and g1 2 x 2 x 2")
+        self = cls.__new__(cls)
+        handle = ctypes.c_void_p()
+        _check(lib().brickwork_create(int(L), g2.view(np.float64).ctypes.data_as(_dptr),
+                                      g1.view(np.float64).ctypes.data_as(_dptr),
+                                      ctypes.byref(handle)), "brickwork_create")
+        self.handle = handle
+        self.L, self.J, self.g, self.h = L, None, None, None
+        d = ctypes.c_int64()
+        _check(lib().floquet_dim(self.handle, ctypes.byref(d)), "floquet_dim")
+        self.d = d.value
+        return self
 
     def close(self):
         if self.handle:
