@@ -179,6 +179,7 @@ struct PassVariant {
   int NB, RB;
   int cols = 0;
   bool pipe = false;
+  bool pair = false;  // the tile is split over a two-CTA cluster (pass_pair.cuh)
 };
 template <typename Real> int num_variants();
 template <typename Real> PassVariant variant_info(int v);

@@ -239,7 +239,7 @@ def test_filter_double_float_matches_oracle(L, k, phi, form):
     assert _rel(from_dev(t_out), want) < 1e-14 * k * (L + 3)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("L", [13, 15, 18, 20])
 def test_every_launch_shape_matches_oracle(variant, L, monkeypatch):
     # the autotuner may pick any launch shape (2, 3 or 4 passes per U); force each one
@@ -268,10 +268,12 @@ def test_every_launch_shape_matches_oracle(variant, L, monkeypatch):
 
 @pytest.mark.parametrize("variant,L", [(4, 18), (4, 19), (4, 20), (4, 21),
                                        (5, 16), (5, 17), (5, 18), (5, 19),
-                                       (6, 20), (6, 21), (7, 18), (7, 20)])
+                                       (6, 20), (6, 21), (7, 18), (7, 20),
+                                       (8, 18), (8, 19), (8, 20), (8, 21)])
 @pytest.mark.parametrize("g", [0.4, 0.9045])   # tan and cot forms of the butterfly
 def test_pipelined_double_float_passes_match_oracle(variant, L, g, monkeypatch):
-    # double-float shapes 4-7 run the persistent cp.async-pipelined pass kernel for the
+    # double-float shapes 4-8 run the persistent cp.async-pipelined pass kernel (shape 8: its
+    # two-CTA cluster form, the tile's top bit exchanged through distributed shared memory) for the
     # first pass and for later passes with 2-4 column bits (L = 21 and 19 add a third pass
     # that falls back to the one-tile-per-CTA kernel); several vectors, in place, and every
     # epilogue (plain phase, accumulate, Horner)
