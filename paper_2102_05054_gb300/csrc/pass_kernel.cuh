@@ -96,6 +96,47 @@ __device__ __forceinline__ float4 zfma(float4 c, float4 v, float4 acc) {
   return make_float4(re.x, re.y, im.x, im.y);
 }
 
+// ------------------------------------------------------------------ last-pass epilogue
+
+// Stores the R amplitudes v[r] that a thread holds at global indices tbase + roff[r] of
+// vector vec: unchanged (EPI_STORE), or times the diagonal phase D_s (the product of the two
+// table entries), followed by the accumulate update acc += coef_j D v or the Horner update
+// dst = psi_in + (z D) v. other(r, s) returns the accumulator or psi_in value of register r.
+template <typename Real, int R, int EPI, typename Other>
+__device__ __forceinline__ void pass_epilogue(const PassArgs<Real>& A, int64_t vec,
+                                              uint32_t tbase, const uint32_t (&roff)[R],
+                                              const cplx<Real> (&v)[R], Other other) {
+  using C = cplx<Real>;
+  C* __restrict__ dst = A.dst + vec * A.d + tbase;
+  if (EPI == EPI_STORE) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[roff[r]] = v[r];
+    return;
+  }
+  const int64_t prob = vec / A.vec_per_prob;
+  const C* __restrict__ tlo = A.tab_lo + (A.lo_by_vec ? vec : prob) * A.tab_lo_stride;
+  const C* __restrict__ thi = A.tab_hi + prob * A.tab_hi_stride;
+  const uint32_t lomask = (1u << A.a) - 1u;
+  const int am1 = A.a - 1;
+  C cj;
+  if (EPI == EPI_PHASE_ACC) cj = A.coef[vec * A.coef_stride + A.jstep];
+  C* __restrict__ acc = A.acc + vec * A.d + tbase;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t s = tbase + roff[r];
+    const C p = zmul(__ldg(&tlo[s & lomask]), __ldg(&thi[((s >> am1) << 1) | (s & 1u)]));
+    if (EPI == EPI_PHASE) {
+      dst[roff[r]] = zmul(p, v[r]);
+    } else if (EPI == EPI_PHASE_ACC) {
+      const C val = zmul(p, v[r]);
+      dst[roff[r]] = val;
+      acc[roff[r]] = zfma(cj, val, other(r, s));
+    } else {  // Horner: dst (= acc) = psi_in + z U acc, z folded into the table
+      dst[roff[r]] = zfma(p, v[r], other(r, s));
+    }
+  }
+}
+
 // ------------------------------------------------------------------ pass kernel
 
 // Tile element e -> position in padded shared memory (one pad slot every 2^RB elements
@@ -216,37 +257,10 @@ __global__ void __launch_bounds__(pass_max_threads<NBT, RB>(), MINB)
     for (int r = 0; r < R; ++r) v[r] = sm[smem_pos<RB>(tile_elem<RB>(t, r, g_top))];
   }
 
-  C* __restrict__ dst = A.dst + vec * A.d;
-  if (EPI == EPI_STORE) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) dst[tbase + roff[r]] = v[r];
-    return;
-  }
-  const int64_t prob = vec / A.vec_per_prob;
-  const C* __restrict__ tlo = A.tab_lo + (A.lo_by_vec ? vec : prob) * A.tab_lo_stride;
-  const C* __restrict__ thi = A.tab_hi + prob * A.tab_hi_stride;
-  const uint32_t lomask = (1u << A.a) - 1u;
-  const int am1 = A.a - 1;
-  C cj;
-  if (EPI == EPI_PHASE_ACC) cj = A.coef[vec * A.coef_stride + A.jstep];
-  C* __restrict__ acc = A.acc + vec * A.d;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const uint32_t s = tbase + roff[r];
-    const C p = zmul(__ldg(&tlo[s & lomask]), __ldg(&thi[((s >> am1) << 1) | (s & 1u)]));
-    const C val = zmul(p, v[r]);
-    if (EPI == EPI_PHASE) {
-      dst[s] = val;
-    } else {
-      const C o = kPrefetch ? pre[kPrefetch ? r : 0] : other[s];
-      if (EPI == EPI_PHASE_ACC) {
-        dst[s] = val;
-        acc[s] = zfma(cj, val, o);
-      } else {  // Horner: dst (= acc) = psi_in + z U acc, z folded into the table
-        dst[s] = zfma(p, v[r], o);
-      }
-    }
-  }
+  pass_epilogue<Real, R, EPI>(A, vec, tbase, roff, v, [&](int r, uint32_t s) -> C {
+    if constexpr (kPrefetch) return pre[r];
+    return other[s];
+  });
 }
 
 template <typename Real, int NBT, int RB, int EPI, bool SWAP, int MINB>

@@ -135,34 +135,8 @@ __global__ void __launch_bounds__(1 << (NBL - RB), MINB)
       for (int r = 0; r < R; ++r) v[r] = cur[p_top + pipe_pos_r<RB>(r, g_top)];
     }
 
-    C* __restrict__ dst = A.dst + vec * A.d + tbase;
-    if (EPI == EPI_STORE) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) dst[roff[r]] = v[r];
-      continue;
-    }
-    const int64_t prob = vec / A.vec_per_prob;
-    const C* __restrict__ tlo = A.tab_lo + (A.lo_by_vec ? vec : prob) * A.tab_lo_stride;
-    const C* __restrict__ thi = A.tab_hi + prob * A.tab_hi_stride;
-    const uint32_t lomask = (1u << A.a) - 1u;
-    const int am1 = A.a - 1;
-    C cj;
-    if (EPI == EPI_PHASE_ACC) cj = A.coef[vec * A.coef_stride + A.jstep];
-    C* __restrict__ acc = A.acc + vec * A.d + tbase;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint32_t s = tbase + roff[r];
-      const C p = zmul(__ldg(&tlo[s & lomask]), __ldg(&thi[((s >> am1) << 1) | (s & 1u)]));
-      const C val = zmul(p, v[r]);
-      if (EPI == EPI_PHASE) {
-        dst[roff[r]] = val;
-      } else if (EPI == EPI_PHASE_ACC) {
-        dst[roff[r]] = val;
-        acc[roff[r]] = zfma(cj, val, pre[kOther ? r : 0]);
-      } else {
-        dst[roff[r]] = zfma(p, v[r], pre[kOther ? r : 0]);
-      }
-    }
+    pass_epilogue<Real, R, EPI>(A, vec, tbase, roff, v,
+                                [&](int r, uint32_t) -> C { return pre[kOther ? r : 0]; });
   }
   cp_async_wait<0>();
 }
