@@ -181,13 +181,15 @@ int arnoldi_eigs(floquet_t op, double phi, int64_t k, int nev, int m, int precis
 
 /* Many independent eigenproblems in lockstep on one GPU: R disorder realisations (h: host,
  * R*L doubles, realisation r at h + r*L) times P targets (phis: host, P doubles), all with
- * the same L, J, g, k, nev, m and the FP64 form. Problem q = r*P + p. v0: host or device,
- * d complex128, shared start vector. Outputs (host): evals 2*nev*R*P doubles, resid
- * nev*R*P, n_conv R*P; problem q's block starts at q*nev. Synchronises `stream`. */
+ * the same L, J, g, k, nev, m. Problem q = r*P + p. precision: FLOQUET_FP64 or
+ * FLOQUET_FILTER_DF (double-float sweeps; FLOQUET_FILTER_FP32 is not offered for batches:
+ * FLOQUET_EINVAL). v0: host or device, d complex128, shared start vector. Outputs (host):
+ * evals 2*nev*R*P doubles, resid nev*R*P, n_conv R*P; problem q's block starts at q*nev.
+ * Synchronises `stream`. */
 int arnoldi_eigs_batched(int L, double J, double g, const double* h, int R,
-                         const double* phis, int P, int64_t k, int nev, int m, double tol,
-                         double tol_resid, int max_restarts, const void* v0, double* evals,
-                         double* resid, int* n_conv, void* stream);
+                         const double* phis, int P, int64_t k, int nev, int m, int precision,
+                         double tol, double tol_resid, int max_restarts, const void* v0,
+                         double* evals, double* resid, int* n_conv, void* stream);
 
 /* The paper's choice of filter length and Krylov dimension (Sec. 4, strategy paragraph;
  * Sec. 5, parameter scan of Fig. bench): the runtime is minimal when the Krylov dimension is

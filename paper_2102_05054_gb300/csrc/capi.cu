@@ -455,16 +455,20 @@ int arnoldi_eigs(floquet_t op, double phi, int64_t k, int nev, int m, int precis
 }
 
 int arnoldi_eigs_batched(int L, double J, double g, const double* h, int R, const double* phis,
-                         int P, int64_t k, int nev, int m, double tol, double tol_resid,
-                         int max_restarts, const void* v0, double* evals, double* resid,
-                         int* n_conv, void* stream) {
+                         int P, int64_t k, int nev, int m, int precision, double tol,
+                         double tol_resid, int max_restarts, const void* v0, double* evals,
+                         double* resid, int* n_conv, void* stream) {
   FQ_GUARD_BEGIN
   if (!h || !phis || !v0 || !evals || !resid || !n_conv || R < 1 || P < 1 || L < 3 || L > 24 ||
       (int64_t)R * P > 65535) {
     set_error("arnoldi_eigs_batched: bad arguments");
     return FLOQUET_EINVAL;
   }
-  FQ_TRY(check_eig_args((int64_t)1 << L, k, nev, m, FLOQUET_FP64, max_restarts));
+  if (precision != FLOQUET_FP64 && precision != FLOQUET_FILTER_DF) {
+    set_error("arnoldi_eigs_batched: precision must be FLOQUET_FP64 or FLOQUET_FILTER_DF");
+    return FLOQUET_EINVAL;
+  }
+  FQ_TRY(check_eig_args((int64_t)1 << L, k, nev, m, precision, max_restarts));
   if (tol <= 0) tol = 1e-12;
   if (tol_resid <= 0) tol_resid = 1e-10;
   floquet_op op;
@@ -473,7 +477,7 @@ int arnoldi_eigs_batched(int L, double J, double g, const double* h, int R, cons
     std::vector<double> ph((size_t)R * P);
     for (int r = 0; r < R; ++r)
       for (int p = 0; p < P; ++p) ph[(size_t)r * P + p] = phis[p];
-    rc = solve_and_copy(&op, R * P, P, ph.data(), k, nev, m, FLOQUET_FP64, tol, tol_resid,
+    rc = solve_and_copy(&op, R * P, P, ph.data(), k, nev, m, precision, tol, tol_resid,
                         max_restarts, v0, evals, nullptr, resid, n_conv, (cudaStream_t)stream);
   }
   op_free(&op);

@@ -44,8 +44,8 @@ SIGNATURES = {
                               _c_double, _c_int, _c_void_p, _dptr, _c_void_p, _dptr, _iptr,
                               _c_void_p]),
     "arnoldi_eigs_batched": (_c_int, [_c_int, _c_double, _c_double, _dptr, _c_int, _dptr, _c_int,
-                                      _c_int64, _c_int, _c_int, _c_double, _c_double, _c_int,
-                                      _c_void_p, _dptr, _dptr, _iptr, _c_void_p]),
+                                      _c_int64, _c_int, _c_int, _c_int, _c_double, _c_double,
+                                      _c_int, _c_void_p, _dptr, _dptr, _iptr, _c_void_p]),
     "floquet_profile_enable": (_c_int, [_c_int]),
     "floquet_profile_read": (_c_int, [_dptr, ctypes.POINTER(_c_int64), _dptr]),
     "floquet_launch_count": (_c_int64, []),
@@ -250,15 +250,16 @@ def small_eig(A, Y=None, stream=None):
 
 
 def arnoldi_eigs_batched(L, J, g, hs, phis, k, nev, m, v0, tol=0.0, tol_resid=0.0,
-                         max_restarts=50, stream=None, check=True):
+                         max_restarts=50, stream=None, check=True, precision=None):
     hs = np.ascontiguousarray(hs, dtype=np.float64)
     phis = np.ascontiguousarray(phis, dtype=np.float64)
     R, P = hs.shape[0], phis.shape[0]
     ev = np.zeros(2 * nev * R * P)
     res = np.zeros(nev * R * P)
     nconv = np.zeros(R * P, dtype=np.int32)
+    prec = FP64 if precision is None else int(precision)
     rc = lib().arnoldi_eigs_batched(int(L), float(J), float(g), _dp(hs), R, _dp(phis), P, int(k),
-                                    int(nev), int(m), float(tol), float(tol_resid),
+                                    int(nev), int(m), prec, float(tol), float(tol_resid),
                                     int(max_restarts), _ptr(v0), _dp(ev), _dp(res),
                                     nconv.ctypes.data_as(_iptr), _stream(stream))
     if check and rc not in (OK, ENOCONV):

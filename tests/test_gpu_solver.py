@@ -156,14 +156,16 @@ def test_arnoldi_eigs_special_case_g0_L16():
     assert res.max() < 1e-10
 
 
-def test_arnoldi_eigs_batched_matches_dense():
+@pytest.mark.parametrize("precision", [0, 2])
+def test_arnoldi_eigs_batched_matches_dense(precision):
     torch = require_gpu()
     from paper_2102_05054_gb300 import floquet
     L, k, nev, m = 10, 64, 8, 48
     hs, _ = inputs.batched_disorder(L, (0.5, 2.0), 2, 10)
     phis = np.array([0.0, math.pi / 2, math.pi])
     v0 = to_dev(inputs.start_vector(L))
-    om, res, nconv, rc = floquet.arnoldi_eigs_batched(L, 1.0, 0.9045, hs, phis, k, nev, m, v0)
+    om, res, nconv, rc = floquet.arnoldi_eigs_batched(L, 1.0, 0.9045, hs, phis, k, nev, m, v0,
+                                                      precision=precision)
     assert rc == 0
     for r in range(hs.shape[0]):
         op = model.KickedIsing(L, 1.0, 0.9045, hs[r])
