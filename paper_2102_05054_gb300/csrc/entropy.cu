@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(kTriThreads) hermitian_tridiag_kernel(
     // p = A22 v, A22 = A[k+1:, k+1:]
     for (int i = t; i < m; i += blockDim.x) {
       double2 acc = make_double2(0, 0);
+#pragma unroll 4
       for (int j = 0; j < m; ++j) {
         const double2 a = A[(int64_t)(k + 1 + j) * n + (k + 1 + i)];
         const double2 vj = v[j];
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(kTriThreads) hermitian_tridiag_kernel(
     // A22 -= v w^H + w v^H
     for (int i = t; i < m; i += blockDim.x) {
       const double2 vi = v[i], wi = p[i];
+#pragma unroll 4
       for (int j = 0; j < m; ++j) {
         const double2 vj = v[j], wj = p[j];
         double2& a = A[(int64_t)(k + 1 + j) * n + (k + 1 + i)];
@@ -232,8 +234,11 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_entropy_kernel(
   double s = 0;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     // the idx-th smallest eigenvalue: the x where the count passes idx
+    // to an absolute width of 1e-16 of the spectral span: an eigenvalue lambda enters the
+    // entropy as -lambda ln lambda, so one below that width changes S by < 1e-14
     double a = lo, b = hi;
-    for (int it = 0; it < 200 && b - a > 4e-16 * fmax(fabs(a), fabs(b)) + 1e-300; ++it) {
+    const double width = 1e-16 * fmax(span, 1.0);
+    for (int it = 0; it < 100 && b - a > width; ++it) {
       const double mid = 0.5 * (a + b);
       if (sturm_count(dg, e2, n, mid) > idx) b = mid;
       else a = mid;
