@@ -11,6 +11,8 @@
  *   U = D K,  K = exp(-i g sum_i X_i),  D = exp(-i sum_i (J Z_i Z_{i+1} + h_i Z_i)),
  *   periodic chain of L qubits (bond (L-1, 0) included), 3 <= L <= 24.
  *   Amplitude index s = sum_i b_i 2^i (qubit i = bit i), Z|0> = +|0>.
+ * The paper's own operator, a brickwork circuit of two-qubit gates (Sec. 2), is available
+ * through brickwork_create; its handle works with the same calls in complex128 / FP64.
  *
  * Filter length: k is the NUMBER OF TERMS, g_k(U) = sum_{j=0}^{k-1} exp(-i j phi) U^j.
  * (The paper's order-k filter, Eq. geo, has k+1 terms.)
