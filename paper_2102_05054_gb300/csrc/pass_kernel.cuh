@@ -2,11 +2,27 @@
 // translation units pass_f32.cu, pass_f64.cu and pass_df.cu.
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 
 #include "floquet_internal.cuh"
 
 namespace fq {
+
+// The shared-memory opt-in above 48 KiB (cudaFuncSetAttribute) holds per device: remember,
+// for one kernel instantiation, the devices on which it has been set (bit i = device i). The
+// first launch on a device sets it, outside any stream capture (the autotuner launches every
+// shape before a filter graph is captured).
+template <typename K>
+static int opt_in_smem(K kernel, size_t smem, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  FQ_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit && (done.load() & bit)) return FLOQUET_OK;
+  FQ_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  done.fetch_or(bit);
+  return FLOQUET_OK;
+}
 
 // ------------------------------------------------------------------ double-float arithmetic
 
@@ -268,15 +284,9 @@ static int launch_pass_t(const PassArgs<Real>& a, int nvec, cudaStream_t st) {
   const int threads = 1 << (a.NB - RB);
   const size_t smem = (size_t)((1 << a.NB) + (1 << (a.NB - RB))) * sizeof(cplx<Real>);
   if (smem > 48 * 1024) {
-    // tiles above 48 KiB (2^12 complex128 / double-float) need the opt-in carve-out; set once
-    // per instantiation, outside any stream capture (the autotuner launches every variant
-    // before a filter graph is captured)
-    static bool attr_set = false;
-    if (!attr_set) {
-      FQ_CUDA(cudaFuncSetAttribute(pass_kernel<Real, NBT, RB, EPI, SWAP, MINB>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr_set = true;
-    }
+    // tiles above 48 KiB (2^12 complex128 / double-float) need the opt-in carve-out
+    static std::atomic<uint64_t> opted{0};
+    FQ_TRY(opt_in_smem(pass_kernel<Real, NBT, RB, EPI, SWAP, MINB>, smem, opted));
   }
   const int64_t ntiles = (int64_t)1 << (a.L - a.NB);
   if (ntiles * nvec > 0x7fffffffLL) {

@@ -159,13 +159,10 @@ static int launch_pair_t(const PassArgs<Real>& a, int nvec, cudaStream_t st) {
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   if (smem > 48 * 1024) {
-    static bool attr_set = false;
-    if (!attr_set) {
-      FQ_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-      attr_set = true;
-    }
+    static std::atomic<uint64_t> opted{0};
+    FQ_TRY(opt_in_smem(kernel, smem, opted));
   }
+
   const int64_t total = ((int64_t)1 << (a.L - (NBL + 1))) * nvec;
   if (total > 0x3fffffffLL) {
     set_error("launch_pass: grid too large (nvec %d)", nvec);

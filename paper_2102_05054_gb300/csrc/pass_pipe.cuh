@@ -202,15 +202,10 @@ static int launch_pipe_t(const PassArgs<Real>& a, int nvec, cudaStream_t st) {
   constexpr size_t smem = 2 * (size_t)((1 << NB) + (1 << (NB - RB))) * sizeof(cplx<Real>);
   auto kernel = pass_pipe_kernel<Real, NB, RB, KF, EPI, SWAP, pipe_min_blocks<EPI, threads, RB, smem>()>;
   if (smem > 48 * 1024) {
-    // set once per instantiation, outside any stream capture (the autotuner launches every
-    // shape before a filter graph is captured)
-    static bool attr_set = false;
-    if (!attr_set) {
-      FQ_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-      attr_set = true;
-    }
+    static std::atomic<uint64_t> opted{0};
+    FQ_TRY(opt_in_smem(kernel, smem, opted));
   }
+
   const int64_t total = ((int64_t)1 << (a.L - NB)) * nvec;
   if (total > 0x7fffffffLL) {
     set_error("launch_pass: grid too large (nvec %d)", nvec);
