@@ -153,28 +153,32 @@ void brick_free(BrickOp* b) {
   cudaFree(b->UL);
   cudaFree(b->UR);
   cudaFree(b->tmp);
+  cudaFree(b->apply_tmp);
   cudaFree(b->consts);
   cudaFree(b->ws);
   delete b;
 }
 
-int brick_reserve(BrickOp* b, int nvec) {
-  const size_t need = (size_t)nvec << b->L;
-  if (b->tmp_elems >= need) return FLOQUET_OK;
-  cudaFree(b->tmp);
-  b->tmp = nullptr;
-  b->tmp_elems = 0;
-  if (cudaMalloc(&b->tmp, need * sizeof(double2)) != cudaSuccess) {
+static int grow(double2** p, size_t* elems, size_t need) {
+  if (*elems >= need) return FLOQUET_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *elems = 0;
+  if (cudaMalloc(p, need * sizeof(double2)) != cudaSuccess) {
     cudaGetLastError();
     set_error("brickwork: cudaMalloc of %zu bytes failed", need * sizeof(double2));
     return FLOQUET_ENOMEM;
   }
-  b->tmp_elems = need;
+  *elems = need;
   return FLOQUET_OK;
 }
 
+int brick_reserve(BrickOp* b, int nvec) {
+  return grow(&b->tmp, &b->tmp_elems, (size_t)nvec << b->L);
+}
+
 // tmp_v = psi_v U_R^T for every vector (psi_v as a column-major 2^q x d_R matrix)
-static int gemm_right(BrickOp* b, const double2* in, int nvec, cudaStream_t st) {
+static int gemm_right(BrickOp* b, const double2* in, double2* tmp, int nvec, cudaStream_t st) {
   cublasHandle_t h = (cublasHandle_t)b->cublas;
   const int64_t d = (int64_t)1 << b->L, m = (int64_t)1 << b->q;
   const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
@@ -183,13 +187,13 @@ static int gemm_right(BrickOp* b, const double2* in, int nvec, cudaStream_t st) 
   FQ_CUBLAS(cublasZgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_T, (int)m, (int)b->dR,
                                       (int)b->dR, &one, (const cuDoubleComplex*)in, (int)m, d,
                                       (const cuDoubleComplex*)b->UR, (int)b->dR, 0, &zero,
-                                      (cuDoubleComplex*)b->tmp, (int)m, d, nvec));
+                                      (cuDoubleComplex*)tmp, (int)m, d, nvec));
   count_launch();
   return FLOQUET_OK;
 }
 
 // out_v = U_L tmp_v (tmp_v as a column-major d_L x (d / d_L) matrix)
-static int gemm_left(BrickOp* b, double2* out, int nvec, cudaStream_t st) {
+static int gemm_left(BrickOp* b, const double2* tmp, double2* out, int nvec, cudaStream_t st) {
   cublasHandle_t h = (cublasHandle_t)b->cublas;
   const int64_t d = (int64_t)1 << b->L, n = d / b->dL;
   const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
@@ -197,7 +201,7 @@ static int gemm_left(BrickOp* b, double2* out, int nvec, cudaStream_t st) {
   FQ_CUBLAS(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST));
   FQ_CUBLAS(cublasZgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)b->dL, (int)n,
                                       (int)b->dL, &one, (const cuDoubleComplex*)b->UL,
-                                      (int)b->dL, 0, (const cuDoubleComplex*)b->tmp,
+                                      (int)b->dL, 0, (const cuDoubleComplex*)tmp,
                                       (int)b->dL, d, &zero, (cuDoubleComplex*)out,
                                       (int)b->dL, d, nvec));
   count_launch();
@@ -205,9 +209,9 @@ static int gemm_left(BrickOp* b, double2* out, int nvec, cudaStream_t st) {
 }
 
 int brick_apply(BrickOp* b, const double2* in, double2* out, int nvec, cudaStream_t st) {
-  FQ_TRY(brick_reserve(b, nvec));
-  FQ_TRY(gemm_right(b, in, nvec, st));
-  return gemm_left(b, out, nvec, st);
+  FQ_TRY(grow(&b->apply_tmp, &b->apply_tmp_elems, (size_t)nvec << b->L));
+  FQ_TRY(gemm_right(b, in, b->apply_tmp, nvec, st));
+  return gemm_left(b, b->apply_tmp, out, nvec, st);
 }
 
 // Horner step: acc_v = psi_in_v + z_v U acc_v (z_v: device, one per vector)
@@ -215,7 +219,7 @@ int brick_horner_step(BrickOp* b, double2* acc, const double2* psi_in, const dou
                       int nvec, cudaStream_t st) {
   cublasHandle_t h = (cublasHandle_t)b->cublas;
   const int64_t d = (int64_t)1 << b->L, n = d / b->dL;
-  FQ_TRY(gemm_right(b, acc, nvec, st));
+  FQ_TRY(gemm_right(b, acc, b->tmp, nvec, st));
   FQ_CUDA(cudaMemcpyAsync(acc, psi_in, sizeof(double2) * d * nvec, cudaMemcpyDeviceToDevice,
                           st));
   FQ_CUBLAS(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_DEVICE));
@@ -236,8 +240,8 @@ int brick_acc_step(BrickOp* b, double2* work, double2* acc, const double2* coef,
                    int64_t coef_stride, int j, int nvec, cudaStream_t st) {
   cublasHandle_t h = (cublasHandle_t)b->cublas;
   const int64_t d = (int64_t)1 << b->L;
-  FQ_TRY(gemm_right(b, work, nvec, st));
-  FQ_TRY(gemm_left(b, work, nvec, st));
+  FQ_TRY(gemm_right(b, work, b->tmp, nvec, st));
+  FQ_TRY(gemm_left(b, b->tmp, work, nvec, st));
   FQ_CUBLAS(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_DEVICE));
   for (int v = 0; v < nvec; ++v) {
     FQ_CUBLAS(cublasZaxpy(h, (int)d, (const cuDoubleComplex*)(coef + v * coef_stride + j),

@@ -233,8 +233,10 @@ struct BrickOp {
   int64_t dL = 0, dR = 0;          // 2^(q+1), 2^(L-q)
   double2* UL = nullptr;           // dL x dL, column-major
   double2* UR = nullptr;           // dR x dR, column-major
-  double2* tmp = nullptr;          // GEMM intermediate, nvec x d
-  size_t tmp_elems = 0;
+  double2* tmp = nullptr;          // GEMM intermediate of the filter loops (captured in
+  size_t tmp_elems = 0;            // graphs: grown only with the graphs dropped)
+  double2* apply_tmp = nullptr;    // GEMM intermediate of plain U applications
+  size_t apply_tmp_elems = 0;
   double2* consts = nullptr;       // device (1, 0) for the device-pointer GEMMs
   void* cublas = nullptr;          // cublasHandle_t
   void* ws = nullptr;              // cuBLAS workspace (fixed, so no GEMM allocates)

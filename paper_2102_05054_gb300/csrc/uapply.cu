@@ -550,6 +550,13 @@ static int ensure_workspace(floquet_op* op, size_t bytes) {
   return FLOQUET_OK;
 }
 
+// The brickwork GEMM scratch, grown before a filter loop is captured; cached graphs hold the
+// old buffer's address, so they are dropped when it grows.
+static int brick_reserve_for_graphs(floquet_op* op, int nvec) {
+  if (op->brick->tmp_elems < ((size_t)nvec << op->L)) destroy_graphs(op);
+  return brick_reserve(op->brick, nvec);
+}
+
 static FilterGraph* find_graph(floquet_op* op, int64_t k, int nvec, int dtype, int form,
                                const void* coef, int vpp) {
   for (auto& g : op->graphs)
@@ -642,7 +649,7 @@ int filter_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio
   FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
   C* work = reinterpret_cast<C*>(op->work);
   C* acc = reinterpret_cast<C*>(op->acc);
-  if (op->brick) FQ_TRY(brick_reserve(op->brick, nvec));  // before any capture
+  if (op->brick) FQ_TRY(brick_reserve_for_graphs(op, nvec));  // before any capture
   FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, work, acc, coef, k, d, nvec, st)));
   const int np = op->brick ? 2 + nvec : (int)plan_of<Real>(op).passes.size();
   auto body = [&](cudaStream_t s) -> int {
@@ -686,7 +693,7 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
     if constexpr (std::is_same<Real, double>::value) {
       // brickwork: acc = psi_in + z U acc with U as two GEMMs, z as the second GEMM's alpha
       FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
-      FQ_TRY(brick_reserve(op->brick, nvec));  // before any capture
+      FQ_TRY(brick_reserve_for_graphs(op, nvec));  // before any capture
       C* bpin = reinterpret_cast<C*>(op->psi_in_copy);
       C* bacc = reinterpret_cast<C*>(op->acc);
       FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, bpin, bacc, nullptr, 0, d, nvec, st)));

@@ -102,3 +102,31 @@ def test_brickwork_rejects_other_precisions():
     v0 = to_dev(inputs.start_vector(6))
     with pytest.raises(RuntimeError):
         fq.arnoldi_eigs(0.0, 16, 4, 16, v0, precision=floquet.FILTER_DF)
+
+
+def test_brickwork_cached_filter_graphs_survive_scratch_growth():
+    # a cached one-vector filter graph must stay valid after a wider filter and after a plain
+    # U application on many vectors have grown the operator's GEMM scratch
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    L, k = 8, 9
+    fq, op = _make(L, 80)
+    y = inputs.complex_gaussian(1 << L, 81)
+    want = geosum.filter_acc(op, y, 0.3, k)
+
+    def filt(vecs):
+        t_in = to_dev(vecs)
+        t_out = torch.empty_like(t_in)
+        fq.filter_apply(0.3, k, t_in, t_out, form=floquet.FORM_HORNER)
+        torch.cuda.synchronize()
+        return from_dev(t_out, 1 << L)
+
+    assert _rel(filt(y), want) < 1e-13
+    wide = np.stack([y] * 5, axis=1)
+    got = filt(wide)
+    assert max(_rel(got[:, j], want) for j in range(5)) < 1e-13
+    X = inputs.random_states(1 << L, 40, 82)
+    t = to_dev(X)
+    fq.apply_u(t, torch.empty_like(t))
+    torch.cuda.synchronize()
+    assert _rel(filt(y), want) < 1e-13
