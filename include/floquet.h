@@ -175,7 +175,9 @@ int ritz_residuals(floquet_t op, const void* X, int nvec, double* omega, double*
  *   v0          -- host or device, d complex128 start vector (need not be normalised).
  * Outputs: evals host 2*nev doubles (re, im), sorted by closeness; evecs host or device
  * d*nev complex128 (may be NULL); resid host nev doubles; n_conv host int: number of
- * returned pairs meeting tol_resid. 1 <= nev < m <= min(d, 512), 2 <= k <= 2^24.
+ * returned pairs meeting tol_resid. A pair the solver did not find (FLOQUET_ENOCONV, e.g.
+ * a start vector inside an invariant subspace smaller than nev) is returned as eigenvalue 0
+ * with residual +infinity. 1 <= nev < m <= min(d, 512), 2 <= k <= 2^24.
  * Synchronises `stream`. */
 int arnoldi_eigs(floquet_t op, double phi, int64_t k, int nev, int m, int precision,
                  double tol, double tol_resid, int max_restarts, const void* v0,

@@ -110,7 +110,7 @@ def _solve(L, J, g, W, seed, phi, k, nev, m, precision=0, **kw):
     v0 = to_dev(inputs.start_vector(L))
     ev = torch.empty((nev, 1 << L), dtype=torch.complex128, device="cuda")
     om, res, nconv, rc = fq.arnoldi_eigs(phi, k, nev, m, v0, precision=precision, evecs=ev, **kw)
-    return om, res, nconv, rc, from_dev(ev, 1 << L), op
+    return om, res, nconv, rc, from_dev(ev, 1 << L).reshape(1 << L, nev), op
 
 
 def _check_against_dense(om, res, X, op, phi, nev, tol_l=1e-10, tol_ov=1e-9, tol_r=1e-10):
@@ -203,3 +203,64 @@ def test_arnoldi_eigs_with_paper_params_L12(precision):
                                        precision=precision)
     assert rc == 0 and nconv == 24
     _check_against_dense(om, res, X, op, 0.4, 24)
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("L,nev,m,k,phi", [(3, 1, 7, 2, 0.0), (3, 2, 8, 4, 1.0),
+                                           (4, 3, 8, 3, math.pi), (5, 2, 24, 4, -math.pi),
+                                           (8, 1, 12, 16, 2.0)])
+def test_arnoldi_eigs_degenerate_sizes(L, nev, m, k, phi, precision):
+    # the smallest chain (d = 8), one pair, the shortest filter (k = 2 terms), the target
+    # at +-pi, and Krylov dimensions up to the space dimension (m = d: the Krylov space is
+    # the whole space, the last basis vector is zero). With a filter this weak and a tiny
+    # Krylov space (say k = 2, m = 4 of d = 8) the |g_k| ratios are close to one and the
+    # solve may end with FLOQUET_ENOCONV: that is the method's limit, not tested here.
+    om, res, nconv, rc, X, op = _solve(L, 1.0, 0.9045, 1.0, 20 + L, phi, k, nev, m,
+                                       precision=precision)
+    assert rc == 0 and nconv == nev
+    _check_against_dense(om, res, X, op, phi, nev)
+
+
+def test_arnoldi_eigs_restart_limit_returns_partial():
+    # max_restarts = 0 with a Krylov space too small to converge: FLOQUET_ENOCONV, the
+    # converged count and the pairs found so far are reported, nothing is left running
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    L = 11
+    fq = floquet.Floquet(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 4))
+    v0 = to_dev(inputs.start_vector(L))
+    om, res, nconv, rc = fq.arnoldi_eigs(0.0, 16, 12, 20, v0, max_restarts=0)
+    assert rc == floquet.ENOCONV
+    assert 0 <= nconv < 12
+    # the operator stays usable
+    om2, res2, nconv2, rc2 = fq.arnoldi_eigs(0.0, 128, 12, 30, v0)
+    assert rc2 == 0 and nconv2 == 12 and res2.max() <= 1e-10
+    _ = torch
+
+
+def test_arnoldi_eigs_invariant_start_vector():
+    # g = 0: U is diagonal, and a start vector on one basis state spans an invariant Krylov
+    # space of dimension 1 (exact breakdown, beta = 0). One pair is found exactly; asking for
+    # two cannot succeed from this start: the call reports it without NaN or a fault
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    L = 6
+    h = inputs.disorder(L, 1.0, 7)
+    fq = floquet.Floquet(L, 1.0, 0.0, h)
+    lam = model.spectrum_g0(L, 1.0, h)
+    e0 = np.zeros(1 << L, dtype=np.complex128)
+    e0[5] = 1
+    v0 = to_dev(e0)
+    # the target sits on that eigenvalue, so it is inside the filter's main lobe (a value
+    # outside the lobe is never certified as the closest)
+    phi = float(np.angle(lam[5]))
+    om, res, nconv, rc = fq.arnoldi_eigs(phi, 8, 1, 10, v0, max_restarts=3, check=False)
+    assert rc == 0 and nconv == 1
+    assert abs(om[0] - lam[5]) < 1e-12 and res[0] < 1e-12
+    om, res, nconv, rc = fq.arnoldi_eigs(phi, 8, 2, 10, v0, max_restarts=3, check=False)
+    assert rc == floquet.ENOCONV and nconv <= 1
+    # no NaN: a pair that was not found is marked by eigenvalue 0 and residual +inf
+    assert not np.any(np.isnan(om)) and not np.any(np.isnan(res))
+    for w, r in zip(om, res):
+        assert (abs(abs(w) - 1) < 1e-12 and r < 1e-12) or (w == 0 and np.isinf(r))
+    _ = torch
