@@ -12,7 +12,7 @@
  *   periodic chain of L qubits (bond (L-1, 0) included), 3 <= L <= 24.
  *   Amplitude index s = sum_i b_i 2^i (qubit i = bit i), Z|0> = +|0>.
  * The paper's own operator, a brickwork circuit of two-qubit gates (Sec. 2), is available
- * through brickwork_create; its handle works with the same calls in complex128 / FP64.
+ * through brickwork_create; its handle works with the same calls (see there).
  *
  * Filter length: k is the NUMBER OF TERMS, g_k(U) = sum_{j=0}^{k-1} exp(-i j phi) U^j.
  * (The paper's order-k filter, Eq. geo, has k+1 terms.)
@@ -93,10 +93,13 @@ enum floquet_form { FLOQUET_FORM_ACC = 0, FLOQUET_FORM_HORNER = 1 };
  * draws them from the Haar measure). The matrix-free product is the paper's Eq. matvec: U is
  * split at an odd qubit q into U_L (qubits 0..q) and U_R (qubits q..L-1), U = (U_L x 1)
  * (1 x U_R), both built here as dense float64 matrices of side 2^(q+1) and 2^(L-q), and
- * every U application is two complex GEMMs (cuBLAS ZGEMM) on two reshapes of the state.
- * The returned handle works with floquet_apply_u, filter_apply, ritz_residuals and
- * arnoldi_eigs in complex128 / FLOQUET_FP64 only (other dtypes and precisions:
- * FLOQUET_EINVAL). Allocates U_L, U_R and a 32 MiB cuBLAS workspace on the current device. */
+ * every U application is two complex GEMMs on two reshapes of the state (cuBLAS ZGEMM for
+ * complex128; for FLOQUET_C128_DF this library's split-K double-float GEMM on the FP32
+ * pipes). The returned handle works with floquet_apply_u (complex128), filter_apply
+ * (complex128 in both forms, double-float in the Horner form), ritz_residuals and
+ * arnoldi_eigs (FLOQUET_FP64 or FLOQUET_FILTER_DF); other dtypes, forms and precisions give
+ * FLOQUET_EINVAL. Allocates U_L, U_R (float64 and double-float) and a 32 MiB cuBLAS
+ * workspace on the current device. */
 int brickwork_create(int L, const double* g2, const double* g1, floquet_t* out);
 
 /* Create the operator U = D K (Sec. 2; model fixed above). h: host, L doubles, copied.

@@ -237,6 +237,10 @@ struct BrickOp {
   size_t tmp_elems = 0;            // graphs: grown only with the graphs dropped)
   double2* apply_tmp = nullptr;    // GEMM intermediate of plain U applications
   size_t apply_tmp_elems = 0;
+  float4* ULdf = nullptr;          // U_L and U_R in double-float, for the double-float sweeps
+  float4* URdf = nullptr;
+  float4* part = nullptr;          // split-K partial sums of the double-float GEMMs (captured
+  size_t part_elems = 0;           // in graphs like tmp: grown only with the graphs dropped)
   double2* consts = nullptr;       // device (1, 0) for the device-pointer GEMMs
   void* cublas = nullptr;          // cublasHandle_t
   void* ws = nullptr;              // cuBLAS workspace (fixed, so no GEMM allocates)
@@ -291,6 +295,10 @@ int brick_reserve(BrickOp* b, int nvec);
 int brick_apply(BrickOp* b, const double2* in, double2* out, int nvec, cudaStream_t st);
 int brick_horner_step(BrickOp* b, double2* acc, const double2* psi_in, const double2* zs,
                       int nvec, cudaStream_t st);
+// double-float sweeps: reserve (outside any capture) and one Horner step
+int brick_reserve_df(BrickOp* b, int nvec);
+int brick_horner_step_df(BrickOp* b, float4* acc, const float4* psi_in, const float4* zs,
+                         int nvec, cudaStream_t st);
 int brick_acc_step(BrickOp* b, double2* work, double2* acc, const double2* coef,
                    int64_t coef_stride, int j, int nvec, cudaStream_t st);
 

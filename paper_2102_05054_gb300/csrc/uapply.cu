@@ -706,8 +706,28 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
         FQ_TRY(run_loop(op, use_graph, k, nvec, sweep_dtype<Real>(), FLOQUET_FORM_HORNER, zs,
                         vec_per_prob, (k - 1) * (1 + nvec), st, bbody));
       return launch_convert_strided<Real, Rio>(bacc, out, out_stride, d, nvec, st);
+    } else if constexpr (std::is_same<Real, dfloat>::value) {
+      // brickwork in double-float: the split-K GEMMs of brickwork.cu, z folded into the
+      // second product's epilogue
+      FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
+      if (op->brick->tmp_elems < ((size_t)nvec << op->L)) destroy_graphs(op);
+      const BrickOp before = *op->brick;
+      FQ_TRY(brick_reserve_df(op->brick, nvec));  // before any capture
+      if (op->brick->part != before.part || op->brick->tmp != before.tmp) destroy_graphs(op);
+      C* bpin = reinterpret_cast<C*>(op->psi_in_copy);
+      C* bacc = reinterpret_cast<C*>(op->acc);
+      FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, bpin, bacc, nullptr, 0, d, nvec, st)));
+      auto bbody = [&](cudaStream_t s) -> int {
+        for (int64_t j = 1; j < k; ++j)
+          FQ_TRY(brick_horner_step_df(op->brick, bacc, bpin, zs, nvec, s));
+        return FLOQUET_OK;
+      };
+      if (k > 1)
+        FQ_TRY(run_loop(op, use_graph, k, nvec, sweep_dtype<Real>(), FLOQUET_FORM_HORNER, zs,
+                        vec_per_prob, (k - 1) * 4, st, bbody));
+      return launch_convert_strided<Real, Rio>(bacc, out, out_stride, d, nvec, st);
     } else {
-      set_error("brickwork operator: complex128 sweeps only");
+      set_error("brickwork operator: complex128 or double-float sweeps only");
       return FLOQUET_EINVAL;
     }
   }

@@ -101,7 +101,11 @@ def test_brickwork_rejects_other_precisions():
         fq.apply_u(x, torch.empty_like(x))
     v0 = to_dev(inputs.start_vector(6))
     with pytest.raises(RuntimeError):
-        fq.arnoldi_eigs(0.0, 16, 4, 16, v0, precision=floquet.FILTER_DF)
+        fq.arnoldi_eigs(0.0, 16, 4, 16, v0, precision=floquet.FILTER_FP32)
+    y = to_dev(inputs.complex_gaussian(64, 2))
+    with pytest.raises(RuntimeError):  # the accumulate form has no double-float GEMM path
+        fq.filter_apply(0.1, 4, y, torch.empty_like(y), form=floquet.FORM_ACC,
+                        sweep=floquet.C128_DF)
 
 
 def test_brickwork_cached_filter_graphs_survive_scratch_growth():
@@ -130,3 +134,37 @@ def test_brickwork_cached_filter_graphs_survive_scratch_growth():
     fq.apply_u(t, torch.empty_like(t))
     torch.cuda.synchronize()
     assert _rel(filt(y), want) < 1e-13
+
+
+@pytest.mark.parametrize("L,k", [(4, 3), (8, 17), (12, 64), (16, 5)])
+def test_brickwork_double_float_filter(L, k):
+    # the double-float split-K GEMMs (FP32 pipes): Horner filter against the oracle; each
+    # U application sums d_L + d_R products per amplitude with ~2^-48 relative rounding
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    fq, op = _make(L, 90 + L)
+    Y = inputs.random_states(1 << L, 2, 91)
+    t_in = to_dev(Y)
+    t_out = torch.empty_like(t_in)
+    fq.filter_apply(0.8, k, t_in, t_out, form=floquet.FORM_HORNER, sweep=floquet.C128_DF)
+    torch.cuda.synchronize()
+    got = from_dev(t_out, 1 << L)
+    for j in range(2):
+        assert _rel(got[:, j], geosum.filter_acc(op, Y[:, j], 0.8, k)) < 1e-13 * k
+
+
+def test_brickwork_eigensolver_double_float_L10():
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    L, nev = 10, 50
+    k, m = floquet.suggest_params(L, nev)
+    fq, op = _make(L, 3)
+    v0 = to_dev(inputs.start_vector(L))
+    ev = torch.empty((nev, 1 << L), dtype=torch.complex128, device="cuda")
+    om, res, nconv, rc = fq.arnoldi_eigs(0.0, k, nev, m, v0, evecs=ev,
+                                         precision=floquet.FILTER_DF)
+    assert rc == 0 and nconv == nev
+    om_d, _, _ = krylov.dense_eigs(op, 0.0, nev)
+    assert np.abs(om - om_d).max() < 1e-10
+    _, r_cpu, _ = krylov.rayleigh_residual(op, from_dev(ev, 1 << L))
+    assert r_cpu.max() <= 1e-10
