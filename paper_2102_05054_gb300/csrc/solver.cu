@@ -472,8 +472,7 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
 // a_l(omega) = z^{l+1} g_{k-1-l}(z omega), l = 0..k-2: the polynomial q with
 // g_k(U) - g_k(omega) = q(U) (U - omega), so that g_k(U) x = g_k(omega) x + q(U) r for
 // r = (U - omega) x. The FP32 sweeps then act on the small residual r only.
-static void defect_coefficients(cd omega, double phi, int64_t k, float2* out,
-                                cd* g_at_omega) {
+static void defect_coefficients(cd omega, double phi, int64_t k, cd* out, cd* g_at_omega) {
   const cd z = std::polar(1.0, -phi);
   const cd w = z * omega;
   // g_n(w) for n = 1 .. k by g_{n} = g_{n-1} + w^{n-1}
@@ -486,8 +485,7 @@ static void defect_coefficients(cd omega, double phi, int64_t k, float2* out,
   }
   *g_at_omega = g[k];
   for (int64_t l = 0; l + 1 < k; ++l) {
-    const cd a = std::polar(1.0, -phi * (double)(l + 1)) * g[k - 1 - l];
-    out[l] = make_float2((float)a.real(), (float)a.imag());
+    out[l] = std::polar(1.0, -phi * (double)(l + 1)) * g[k - 1 - l];
   }
 }
 
@@ -537,6 +535,15 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
   const bool verbose = getenv("FLOQUET_VERBOSE") != nullptr;
   DevBuf<double2> S, WS, Xn, G, Yg, lam, eigw, R, corr;
   DevBuf<float2> coef;
+  DevBuf<float4> coefdf;
+  // the correction filter q(U) r sums k terms of size up to k |r|: complex64 sweeps round it
+  // at ~u32 k relative to the useful part, double-float sweeps at ~2^-48 k. The polish starts
+  // with complex64 (cheaper) and switches to double-float once the worst selected residual
+  // has not halved over three iterations; FLOQUET_POLISH_SWEEP=c64 or =df fixes the choice.
+  const char* psw = getenv("FLOQUET_POLISH_SWEEP");
+  const bool forced = psw && (strcmp(psw, "c64") == 0 || strcmp(psw, "df") == 0);
+  bool df_corr = forced && strcmp(psw, "df") == 0;
+  std::vector<double> worst_hist;
   DevBuf<double> rq;
   DevBuf<int> info;
   FQ_TRY(S.alloc((size_t)n2 * d));
@@ -550,13 +557,18 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
   FQ_TRY(R.alloc((size_t)nb * d));
   FQ_TRY(corr.alloc((size_t)nb * d));
   FQ_TRY(rq.alloc((size_t)3 * n2));
-  FQ_TRY(coef.alloc((size_t)nb * (k - 1)));
+  if (df_corr)
+    FQ_TRY(coefdf.alloc((size_t)nb * (k - 1)));
+  else
+    FQ_TRY(coef.alloc((size_t)nb * (k - 1)));
+  std::vector<float4> coefdf_h(df_corr ? (size_t)nb * (k - 1) : 0);
   const double drop = 1e-6;
   FQ_CUDA(cudaMemcpyAsync(S.p, X0, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
   int ns = 0;
   FQ_TRY(orthonormalize(ws, S.p, nb, d, drop, &ns, st));
   std::vector<double> rq_h(3 * n2);
-  std::vector<float2> coef_h((size_t)nb * (k - 1));
+  std::vector<cd> coef_c((size_t)(k - 1));
+  std::vector<float2> coef_h(df_corr ? 0 : (size_t)nb * (k - 1));
   std::vector<double2> lam_h(n2);
   int nk = 0;
   for (int it = 0;; ++it) {
@@ -635,6 +647,13 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
                 std::abs(gk_value(om[wi], phi, k)), gabs[order[0]], gabs[order[nk - 1]],
                 (int)sel.size());
     }
+    worst_hist.push_back(worst);
+    if (!forced && !df_corr && it >= 3 && !(worst < 0.5 * worst_hist[it - 3])) {
+      df_corr = true;  // complex64 corrections have stalled
+      FQ_TRY(coefdf.alloc((size_t)nb * (k - 1)));
+      coefdf_h.assign((size_t)nb * (k - 1), make_float4(0, 0, 0, 0));
+      if (verbose) fprintf(stderr, "floquet polish: switching to double-float corrections\n");
+    }
     if (worst <= tol_resid || it >= max_iter || nf == 0) {
       FQ_CUDA(cudaMemcpyAsync(X0, Xn.p, sizeof(double2) * nk * d, cudaMemcpyDeviceToDevice, st));
       break;
@@ -646,11 +665,26 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
         FQ_CUDA(cudaMemcpyAsync(R.p + (size_t)j * d, R.p + (size_t)i * d, sizeof(double2) * d,
                                 cudaMemcpyDeviceToDevice, st));
       cd gv;
-      defect_coefficients(om[i], phi, k, coef_h.data() + (size_t)j * (k - 1), &gv);
+      defect_coefficients(om[i], phi, k, coef_c.data(), &gv);
+      for (int64_t l = 0; l + 1 < k; ++l) {
+        const size_t o = (size_t)j * (k - 1) + l;
+        if (df_corr)
+          coefdf_h[o] = from_d2<dfloat>(make_double2(coef_c[l].real(), coef_c[l].imag()));
+        else
+          coef_h[o] = make_float2((float)coef_c[l].real(), (float)coef_c[l].imag());
+      }
     }
-    FQ_CUDA(cudaMemcpyAsync(coef.p, coef_h.data(), sizeof(float2) * (size_t)nf * (k - 1),
-                            cudaMemcpyHostToDevice, st));
-    FQ_TRY((filter_coef<float, double>(op, R.p, d, corr.p, d, coef.p, k - 1, nf, nf, true, st)));
+    if (df_corr) {
+      FQ_CUDA(cudaMemcpyAsync(coefdf.p, coefdf_h.data(), sizeof(float4) * (size_t)nf * (k - 1),
+                              cudaMemcpyHostToDevice, st));
+      FQ_TRY((filter_coef<dfloat, double>(op, R.p, d, corr.p, d, coefdf.p, k - 1, nf, nf, true,
+                                          st)));
+    } else {
+      FQ_CUDA(cudaMemcpyAsync(coef.p, coef_h.data(), sizeof(float2) * (size_t)nf * (k - 1),
+                              cudaMemcpyHostToDevice, st));
+      FQ_TRY((filter_coef<float, double>(op, R.p, d, corr.p, d, coef.p, k - 1, nf, nf, true,
+                                         st)));
+    }
     // span(S) = span(Xn, g_k(U) Xn_active) = span(Xn, corr_active)
     FQ_CUDA(cudaMemcpyAsync(S.p, Xn.p, sizeof(double2) * nk * d, cudaMemcpyDeviceToDevice, st));
     FQ_CUDA(cudaMemcpyAsync(S.p + (size_t)nk * d, corr.p, sizeof(double2) * nf * d,
