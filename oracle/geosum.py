@@ -74,3 +74,18 @@ def gk_on_circle(theta, phi, k):
     nz = np.abs(den) > 1e-300
     out[nz] = np.abs(num[nz] / den[nz])
     return out
+
+
+def defect_coefficients(omega, phi, k):
+    """Coefficients a_l (l = 0 .. k-2) of q(U) = sum_l a_l U^l with
+    g_k(U) - g_k(omega) = q(U) (U - omega), z = exp(-i phi).
+
+    Follows from Eq. geo term by term: z^j (U^j - omega^j) = z^j (U - omega) sum_{m<j}
+    U^m omega^{j-1-m}; collecting the power U^l over j > l gives
+    a_l = z^{l+1} sum_{j=0}^{k-2-l} (z omega)^j = z^{l+1} g_{k-1-l}(z omega) with g_n the
+    n-term geometric sum at phase 0. Used by the FP64 polish of the FP32-filter form
+    (g_k(U) x = g_k(omega) x + q(U) r, r = (U - omega) x)."""
+    z = np.exp(-1j * phi)
+    w = z * complex(omega)
+    g = np.concatenate([[0.0 + 0j], np.cumsum(w ** np.arange(k))])  # g[n] = sum_{j<n} w^j
+    return np.array([z ** (l + 1) * g[k - 1 - l] for l in range(k - 1)], dtype=np.complex128)

@@ -535,3 +535,23 @@ def test_brickwork_product_gates_spectrum():
     got = np.linalg.eigvals(op.dense())
     for x in lam:
         assert np.min(np.abs(got - x)) < 1e-12
+
+
+def test_defect_coefficients_identity():
+    # g_k(U) x - g_k(omega) x = q(U) (U - omega) x for any x and any complex omega (not only
+    # eigenvalues), checked with dense U; a wrong power or a dropped z fails it
+    L, k, phi = 6, 12, 0.7
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 12))
+    U = op.dense()
+    x = inputs.complex_gaussian(1 << L, 5)
+    for omega in (np.exp(0.3j), 0.9 * np.exp(-2.0j), 1.1 + 0.2j):
+        a = geosum.defect_coefficients(omega, phi, k)
+        assert a.shape == (k - 1,)
+        lhs = geosum.filter_dense(U, phi, k) @ x - geosum.gk_closed(omega, phi, k) * x
+        r = U @ x - omega * x
+        rhs = np.zeros_like(x)
+        p = r.copy()
+        for coef in a:  # sum_l a_l U^l r
+            rhs += coef * p
+            p = U @ p
+        assert np.linalg.norm(lhs - rhs) < 1e-12 * np.linalg.norm(lhs)
