@@ -169,6 +169,10 @@ template <typename Real> struct PassArgs {
   int64_t coef_stride;
   int jstep;
   const cplx<Real>* psi_in;
+  // general Horner coefficients (nullable): the Horner epilogue adds hcoef[vec * hcoef_stride
+  // + jstep] * psi_in instead of psi_in
+  const cplx<Real>* hcoef;
+  int64_t hcoef_stride;
 };
 
 // Launch shapes of the pass kernel that the autotuner chooses from, per sweep precision: the
@@ -264,6 +268,7 @@ struct floquet_op {
   fq::Plan plan[3];
   int variant[3] = {0, 0, 0};
   bool tuned[3] = {false, false, false};
+  int gshape[3] = {-1, -1, -1};  // shape of the persistent Horner kernel (-1: per-pass kernels)
   // filter workspace (lazily sized)
   void* work = nullptr;
   void* acc = nullptr;
@@ -278,6 +283,7 @@ struct floquet_op {
   int coef_dtype = -1, coef_nvec = -1, coef_form = -1;
   std::vector<fq::FilterGraph> graphs;
   cudaStream_t cap_stream = nullptr;  // capture/replay stream of the filter graphs
+  unsigned* bar = nullptr;  // grid-barrier counter and error word of the persistent filter
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
@@ -321,5 +327,13 @@ template <typename Real, typename Rio>
 int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio>* out,
                   int64_t out_stride, const cplx<Real>* zs, int64_t k, int nvec,
                   int vec_per_prob, bool use_graph, cudaStream_t st);
+
+// General Horner evaluation out_v = sum_{l=0}^{k-1} c_l (z_v U)^l in_v with c_{k-1} = 1 and
+// the other coefficients c_l = hcoef[k-1-l] (hcoef: device, k complex of Real, shared by the
+// vectors; hcoef[0] is not read): acc <- in, then acc <- hcoef[j] in + z U acc, j = 1..k-1.
+template <typename Real, typename Rio>
+int filter_horner_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio>* out,
+                       int64_t out_stride, const cplx<Real>* zs, const cplx<Real>* hcoef,
+                       int64_t k, int nvec, cudaStream_t st);
 
 }  // namespace fq

@@ -614,6 +614,27 @@ int axpy_cols(const double2* X, double2* Y, int64_t d, int n, const double2* a,
   return FLOQUET_OK;
 }
 
+// C[:, j] -= T[:, j], j < n (leading dimensions ldc, ldt)
+__global__ void sub_cols_kernel(double2* __restrict__ C, int64_t ldc,
+                                const double2* __restrict__ T, int64_t ldt, int64_t d) {
+  const int j = blockIdx.y;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = C[(int64_t)j * ldc + r], b = T[(int64_t)j * ldt + r];
+    C[(int64_t)j * ldc + r] = make_double2(a.x - b.x, a.y - b.y);
+  }
+}
+
+int sub_cols(double2* C, int64_t ldc, const double2* T, int64_t ldt, int64_t d, int n,
+             cudaStream_t st) {
+  if (n <= 0) return FLOQUET_OK;
+  const unsigned gx = (unsigned)std::min<int64_t>((d + 255) / 256, 1024);
+  sub_cols_kernel<<<dim3(gx, n), 256, 0, st>>>(C, ldc, T, ldt, d);
+  count_launch();
+  FQ_CHECK_LAUNCH();
+  return FLOQUET_OK;
+}
+
 // R[:, j] = W[:, j] - omega_j X[:, j], omega from stats triples (re, im, .)
 __global__ void residual_vectors_kernel(const double2* __restrict__ X,
                                         const double2* __restrict__ W, double2* __restrict__ R,

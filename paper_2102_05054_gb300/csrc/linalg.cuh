@@ -60,6 +60,9 @@ int axpy_cols(const double2* X, double2* Y, int64_t d, int n, const double2* a,
               cudaStream_t st);
 int residual_vectors(const double2* X, const double2* W, double2* R, int64_t d, int n,
                      const double* om3, cudaStream_t st);
+// C[:, j] -= T[:, j] for j < n (d rows; leading dimensions ldc, ldt).
+int sub_cols(double2* C, int64_t ldc, const double2* T, int64_t ldt, int64_t d, int n,
+             cudaStream_t st);
 
 // Small dense eigensolver (one CTA per matrix): A_b (n x n, lda) = Y_b diag(lam_b) Y_b^{-1}.
 // Y has unit-norm columns; eigenvalues in descending modulus. `work` must hold

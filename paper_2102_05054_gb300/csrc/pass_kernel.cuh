@@ -136,6 +136,9 @@ __device__ __forceinline__ void pass_epilogue(const PassArgs<Real>& A, int64_t v
   const int am1 = A.a - 1;
   C cj;
   if (EPI == EPI_PHASE_ACC) cj = A.coef[vec * A.coef_stride + A.jstep];
+  const bool gen = EPI == EPI_PHASE_HORNER && A.hcoef != nullptr;
+  C hc;
+  if (gen) hc = A.hcoef[vec * A.hcoef_stride + A.jstep];
   C* __restrict__ acc = A.acc + vec * A.d + tbase;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -147,8 +150,9 @@ __device__ __forceinline__ void pass_epilogue(const PassArgs<Real>& A, int64_t v
       const C val = zmul(p, v[r]);
       dst[roff[r]] = val;
       acc[roff[r]] = zfma(cj, val, other(r, s));
-    } else {  // Horner: dst (= acc) = psi_in + z U acc, z folded into the table
-      dst[roff[r]] = zfma(p, v[r], other(r, s));
+    } else {  // Horner: dst (= acc) = c_j psi_in + z U acc, z folded into the table
+      const C o = other(r, s);
+      dst[roff[r]] = zfma(p, v[r], gen ? zmul(hc, o) : o);
     }
   }
 }

@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "floquet_internal.cuh"
+#include "horner_grid.cuh"
 
 namespace fq {
 
@@ -402,6 +403,7 @@ void op_free(floquet_op* op) {
   cudaFree(op->psi_in_copy);
   cudaFree(op->zlo);
   cudaFree(op->coef);
+  cudaFree(op->bar);
 }
 
 template <typename Real> static const Plan& plan_of(const floquet_op* op);
@@ -423,7 +425,8 @@ template <typename Real>
 static int u_passes(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int nvec,
                     int vec_per_prob, int epi, cplx<Real>* acc, const cplx<Real>* coef,
                     int64_t coef_stride, int jstep, const cplx<Real>* psi_in, cudaStream_t st,
-                    const cplx<Real>* lo_per_vec = nullptr) {
+                    const cplx<Real>* lo_per_vec = nullptr,
+                    const cplx<Real>* hcoef = nullptr, int64_t hcoef_stride = 0) {
   const Plan& pl = plan_of<Real>(op);
   const int np = (int)pl.passes.size();
   for (int i = 0; i < np; ++i) {
@@ -438,6 +441,8 @@ static int u_passes(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int n
       a.coef_stride = coef_stride;
       a.jstep = jstep;
       a.psi_in = psi_in;
+      a.hcoef = hcoef;
+      a.hcoef_stride = hcoef_stride;
       if (lo_per_vec) {  // one tab_lo per vector (Horner, z folded in)
         a.tab_lo = lo_per_vec;
         a.lo_by_vec = 1;
@@ -451,62 +456,149 @@ static int u_passes(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int n
 
 static void destroy_graphs(floquet_op* op);
 
-// Autotuner: the first U application in a sweep precision on an operator with L >= 14 times
-// every launch shape of that precision (3 warm-up and 10 timed applications of U to one
-// scratch state, CUDA events on the caller's stream) and keeps the fastest; smaller states
-// keep the first shape. It runs before any filter graph of the operator is captured, and
-// drops the operator's cached graphs when it changes the plan.
+// Live test data for the autotuner: a normalised state with varied amplitudes.
+template <typename Real>
+__global__ void tune_fill_kernel(cplx<Real>* __restrict__ x, int64_t n, double scale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = from_d2<Real>(make_double2(scale * cos(0.1 * (double)i), scale * sin(0.37 * (double)i)));
+}
+
+static int ensure_bar(floquet_op* op);
+
+// Persistent Horner kernel arguments for nvec vectors of the operator's own tables (z = 1,
+// vec_per_prob = nvec: one problem).
+template <typename Real>
+static HornerGridArgs<Real> grid_args(floquet_op* op, const cplx<Real>* pin, cplx<Real>* acc,
+                                      const cplx<Real>* tlo, int64_t lo_stride, int64_t k,
+                                      int nvec, int vec_per_prob) {
+  HornerGridArgs<Real> ga;
+  memset(&ga, 0, sizeof(ga));
+  ga.psi_in = pin;
+  ga.t = acc;
+  ga.d = op->d;
+  ga.L = op->L;
+  ga.nvec = nvec;
+  ga.vec_per_prob = vec_per_prob;
+  ga.a = op->tabs.a;
+  ga.tau = scal_from<Real>(op->tau);
+  ga.tab_lo = tlo;
+  ga.lo_stride = lo_stride;
+  ga.tab_hi = thi_of<Real>(op);
+  ga.hi_stride = op->tabs.hi_n;
+  ga.nsteps = k;
+  ga.bar = op->bar;
+  return ga;
+}
+
+// Autotuner: the first U application or filter in a sweep precision on an operator with
+// L >= 13 times the launch choices on the hot path's own work, Horner filter steps
+// acc <- psi_in + z U acc on a live (non-zero) state with the caller's batch width: every
+// per-pass launch shape of the precision (3 warm-up and 10 timed steps) and, where the chain
+// length has one, the persistent kernel (10 steps in one launch after a warm-up launch).
+// The fastest launch shape serves plain U applications and per-pass filters; the persistent
+// kernel serves the Horner filters if it beats that shape. CUDA events on the caller's
+// stream. It runs before any filter graph of the operator is captured and drops the
+// operator's cached graphs when it changes the plan. FLOQUET_PASS_VARIANT=<i> pins a shape
+// and FLOQUET_FILTER_KERNEL=grid|pass the filter kernel, with FLOQUET_GRID_SHAPE=<i> the
+// persistent kernel's shape (profiling, tests).
 template <typename Real> static int tune(floquet_op* op, int nvec, cudaStream_t st) {
   const int t = sweep_dtype<Real>();
   if (op->tuned[t]) return FLOQUET_OK;
   op->tuned[t] = true;
+  const std::vector<HornerGridShape<Real>> gs = horner_grid_shapes<Real>(op->L);
+  const bool has_grid = !gs.empty();
+  op->gshape[t] = has_grid ? 0 : -1;
+  const char* fk = getenv("FLOQUET_FILTER_KERNEL");
+  const bool grid_forced = fk && (strcmp(fk, "grid") == 0 || strcmp(fk, "pass") == 0);
+  if (grid_forced) op->gshape[t] = (has_grid && strcmp(fk, "grid") == 0) ? 0 : -1;
+  if (const char* fs = getenv("FLOQUET_GRID_SHAPE")) {  // pin a persistent shape (tests)
+    const int i = atoi(fs);
+    if (grid_forced && op->gshape[t] >= 0 && i >= 0 && i < (int)gs.size()) op->gshape[t] = i;
+  }
   const int nv = num_variants<Real>();
-  if (const char* forced = getenv("FLOQUET_PASS_VARIANT")) {  // fixed shape, e.g. to profile
+  const char* forced = getenv("FLOQUET_PASS_VARIANT");  // fixed shape, e.g. to profile
+  if (forced) {
     const int v = atoi(forced);
     if (v >= 0 && v < nv && variant_info<Real>(v).NB <= op->L) {
       set_variant<Real>(op, v);
       destroy_graphs(op);
     }
-    return FLOQUET_OK;
   }
-  if (op->L < 13 || nv < 2) return FLOQUET_OK;
+  if (op->L < 13 || (forced && (grid_forced || !has_grid)) || (nv < 2 && !has_grid))
+    return FLOQUET_OK;
   // time with the caller's batch width (capped), since the best tile depends on how many
   // CTAs the whole launch has
   const int nt = std::max(1, std::min(nvec, std::max(1, (int)((int64_t(64) << 20) / op->d))));
   cplx<Real>* buf = nullptr;
-  FQ_CUDA(cudaMalloc(&buf, sizeof(cplx<Real>) * op->d * nt));
-  FQ_CUDA(cudaMemsetAsync(buf, 0, sizeof(cplx<Real>) * op->d * nt, st));
+  FQ_CUDA(cudaMalloc(&buf, 2 * sizeof(cplx<Real>) * op->d * nt));
+  cplx<Real>* pin = buf;
+  cplx<Real>* acc = buf + op->d * nt;
+  tune_fill_kernel<Real><<<grid_for(op->d * nt, 256), 256, 0, st>>>(
+      pin, op->d * nt, 1.0 / std::sqrt((double)op->d));
+  tune_fill_kernel<Real><<<grid_for(op->d * nt, 256), 256, 0, st>>>(
+      acc, op->d * nt, 1.0 / std::sqrt((double)op->d));
+  count_launch(2);
   cudaEvent_t e0, e1;
   FQ_CUDA(cudaEventCreate(&e0));
   FQ_CUDA(cudaEventCreate(&e1));
+  const bool verbose = getenv("FLOQUET_VERBOSE") != nullptr;
   float best = 3.0e38f;
-  int bestv = 0;
+  int bestv = op->variant[t];
   int rc = FLOQUET_OK;
-  for (int v = 0; v < nv && rc == FLOQUET_OK; ++v) {
+  for (int v = 0; v < nv && rc == FLOQUET_OK && !forced; ++v) {
     set_variant<Real>(op, v);
     if (variant_info<Real>(v).NB > op->L) continue;
     for (int i = 0; i < 3 && rc == FLOQUET_OK; ++i)
-      rc = u_passes<Real>(op, buf, buf, nt, nt, EPI_PHASE, nullptr, nullptr, 0, 0, nullptr, st);
+      rc = u_passes<Real>(op, acc, acc, nt, nt, EPI_PHASE_HORNER, nullptr, nullptr, 0, 0, pin,
+                          st);
     cudaEventRecord(e0, st);
     for (int i = 0; i < 10 && rc == FLOQUET_OK; ++i)
-      rc = u_passes<Real>(op, buf, buf, nt, nt, EPI_PHASE, nullptr, nullptr, 0, 0, nullptr, st);
+      rc = u_passes<Real>(op, acc, acc, nt, nt, EPI_PHASE_HORNER, nullptr, nullptr, 0, 0, pin,
+                          st);
     cudaEventRecord(e1, st);
     if (cudaEventSynchronize(e1) != cudaSuccess) rc = FLOQUET_ECUDA;
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (getenv("FLOQUET_VERBOSE"))
-      fprintf(stderr, "floquet tune: L=%d dtype=%d nvec=%d shape (NB=%d, RB=%d): %.2f us per U\n",
-              op->L, t, nt, variant_info<Real>(v).NB, variant_info<Real>(v).RB, 1000.0 * ms / 10);
+    if (verbose)
+      fprintf(stderr, "floquet tune: L=%d dtype=%d nvec=%d shape (NB=%d, RB=%d): %.2f us per "
+              "Horner step\n", op->L, t, nt, variant_info<Real>(v).NB, variant_info<Real>(v).RB,
+              1000.0 * ms / 10);
     if (rc == FLOQUET_OK && ms < best) {
       best = ms;
       bestv = v;
     }
   }
+  if (!forced) set_variant<Real>(op, bestv);
+  if (has_grid && !grid_forced && rc == FLOQUET_OK) {
+    rc = ensure_bar(op);
+    const HornerGridArgs<Real> ga =
+        grid_args<Real>(op, pin, acc, tlo_of<Real>(op), 0, 11, nt, nt);
+    float gbest = 3.0e38f;
+    int gi = -1;
+    for (int i = 0; i < (int)gs.size() && rc == FLOQUET_OK; ++i) {
+      rc = gs[i].launch(ga, op->swap, false, st);
+      cudaEventRecord(e0, st);
+      if (rc == FLOQUET_OK) rc = gs[i].launch(ga, op->swap, false, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = FLOQUET_ECUDA;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (verbose)
+        fprintf(stderr, "floquet tune: L=%d dtype=%d nvec=%d persistent kernel (NB=%d, RB=%d, "
+                "C=%d): %.2f us per Horner step\n", op->L, t, nt, gs[i].NB, gs[i].RB, gs[i].C,
+                1000.0 * ms / 10);
+      if (rc == FLOQUET_OK && ms < gbest) {
+        gbest = ms;
+        gi = i;
+      }
+    }
+    op->gshape[t] = (rc == FLOQUET_OK && (forced || gbest < best)) ? gi : -1;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(st);
   cudaFree(buf);
-  set_variant<Real>(op, bestv);
   destroy_graphs(op);
   return rc;
 }
@@ -547,6 +639,17 @@ static int ensure_workspace(floquet_op* op, size_t bytes) {
     return FLOQUET_ENOMEM;
   }
   op->work_bytes = bytes;
+  return FLOQUET_OK;
+}
+
+// Grid-barrier words of the persistent filter kernel (allocated once per operator).
+static int ensure_bar(floquet_op* op) {
+  if (op->bar) return FLOQUET_OK;
+  if (cudaMalloc(&op->bar, kBarWords * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("filter workspace: cudaMalloc of the barrier words failed");
+    return FLOQUET_ENOMEM;
+  }
   return FLOQUET_OK;
 }
 
@@ -756,6 +859,23 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
       tlo_of<Real>(op), lo_n, vec_per_prob, zs, zlo, nvec * lo_n);
   count_launch();
   FQ_CHECK_LAUNCH();
+  // persistent kernel: the whole loop in one cooperative launch (one grid barrier per U)
+  const int gsi = op->gshape[sweep_dtype<Real>()];
+  if (k > 1 && gsi >= 0) {
+    const std::vector<HornerGridShape<Real>> gshapes = horner_grid_shapes<Real>(op->L);
+    if (gsi < (int)gshapes.size()) {
+      const HornerGridLaunch<Real> gl = gshapes[gsi].launch;
+      FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, nullptr, pin, nullptr, 0, d, nvec,
+                                            st)));
+      FQ_TRY(ensure_bar(op));
+      const HornerGridArgs<Real> ga =
+          grid_args<Real>(op, pin, acc, zlo, lo_n, k, nvec, vec_per_prob);
+      auto gbody = [&](cudaStream_t s) -> int { return gl(ga, op->swap, false, s); };
+      FQ_TRY(run_loop(op, false, k, nvec, sweep_dtype<Real>(), FLOQUET_FORM_HORNER, zs,
+                      vec_per_prob, 1, st, gbody));
+      return launch_convert_strided<Real, Rio>(acc, out, out_stride, d, nvec, st);
+    }
+  }
   FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, pin, acc, nullptr, 0, d, nvec, st)));
   const int np = (int)plan_of<Real>(op).passes.size();
   auto body = [&](cudaStream_t s) -> int {
@@ -769,6 +889,79 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
                     FLOQUET_FORM_HORNER, zs, vec_per_prob, (k - 1) * np, st, body));
   return launch_convert_strided<Real, Rio>(acc, out, out_stride, d, nvec, st);
 }
+
+template <typename Real, typename Rio>
+int filter_horner_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio>* out,
+                       int64_t out_stride, const cplx<Real>* zs, const cplx<Real>* hcoef,
+                       int64_t k, int nvec, cudaStream_t st) {
+  using C = cplx<Real>;
+  const int64_t d = op->d;
+  if (op->brick) {
+    set_error("general Horner filter: kicked-Ising operators only");
+    return FLOQUET_EINVAL;
+  }
+  FQ_TRY(tune<Real>(op, nvec, st));
+  FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
+  C* pin = reinterpret_cast<C*>(op->psi_in_copy);
+  C* acc = reinterpret_cast<C*>(op->acc);
+  const int64_t lo_n = op->tabs.lo_n;
+  const size_t zbytes = (size_t)nvec * lo_n * sizeof(C);
+  if (op->zlo_bytes < zbytes) {
+    destroy_graphs(op);
+    cudaFree(op->zlo);
+    op->zlo = nullptr;
+    op->zlo_bytes = 0;
+    if (cudaMalloc(&op->zlo, zbytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("filter workspace: cudaMalloc of %zu bytes failed", zbytes);
+      return FLOQUET_ENOMEM;
+    }
+    op->zlo_bytes = zbytes;
+  }
+  C* zlo = reinterpret_cast<C*>(op->zlo);
+  scale_lo_kernel<Real><<<grid_for(nvec * lo_n, 256), 256, 0, st>>>(
+      tlo_of<Real>(op), lo_n, nvec, zs, zlo, nvec * lo_n);
+  count_launch();
+  FQ_CHECK_LAUNCH();
+  FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, nullptr, pin, nullptr, 0, d, nvec, st)));
+  if (k > 1) {
+    const int gsi = op->gshape[sweep_dtype<Real>()];
+    const std::vector<HornerGridShape<Real>> gshapes = horner_grid_shapes<Real>(op->L);
+    if (gsi >= 0 && gsi < (int)gshapes.size()) {
+      FQ_TRY(ensure_bar(op));
+      HornerGridArgs<Real> ga = grid_args<Real>(op, pin, acc, zlo, lo_n, k, nvec, nvec);
+      ga.coef = hcoef;
+      ga.coef_stride = 0;
+      const HornerGridLaunch<Real> gl = gshapes[gsi].launch;
+      auto gbody = [&](cudaStream_t s) -> int { return gl(ga, op->swap, true, s); };
+      FQ_TRY(run_loop(op, false, k, nvec, sweep_dtype<Real>(), FLOQUET_FORM_HORNER, hcoef,
+                      nvec, 1, st, gbody));
+    } else {
+      FQ_CUDA(cudaMemcpyAsync(acc, pin, sizeof(C) * nvec * d, cudaMemcpyDeviceToDevice, st));
+      auto body = [&](cudaStream_t s) -> int {
+        for (int64_t j = 1; j < k; ++j)
+          FQ_TRY(u_passes<Real>(op, acc, acc, nvec, nvec, EPI_PHASE_HORNER, nullptr, nullptr, 0,
+                                (int)j, pin, s, zlo, hcoef, 0));
+        return FLOQUET_OK;
+      };
+      FQ_TRY(run_loop(op, false, k, nvec, sweep_dtype<Real>(), FLOQUET_FORM_HORNER, hcoef,
+                      nvec, 0, st, body));
+    }
+  } else {
+    FQ_CUDA(cudaMemcpyAsync(acc, pin, sizeof(C) * nvec * d, cudaMemcpyDeviceToDevice, st));
+  }
+  return launch_convert_strided<Real, Rio>(acc, out, out_stride, d, nvec, st);
+}
+
+template int filter_horner_coef<float, double>(floquet_op*, const double2*, int64_t, double2*,
+                                               int64_t, const float2*, const float2*, int64_t,
+                                               int, cudaStream_t);
+template int filter_horner_coef<dfloat, double>(floquet_op*, const double2*, int64_t, double2*,
+                                                int64_t, const float4*, const float4*, int64_t,
+                                                int, cudaStream_t);
+template int filter_horner_coef<double, double>(floquet_op*, const double2*, int64_t, double2*,
+                                                int64_t, const double2*, const double2*,
+                                                int64_t, int, cudaStream_t);
 
 #define FQ_INST_FILTER(R, RIO)                                                            \
   template int filter_coef<R, RIO>(floquet_op*, const cplx<RIO>*, int64_t, cplx<RIO>*, int64_t, \
