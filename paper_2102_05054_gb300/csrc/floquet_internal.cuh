@@ -284,6 +284,8 @@ struct floquet_op {
   std::vector<fq::FilterGraph> graphs;
   cudaStream_t cap_stream = nullptr;  // capture/replay stream of the filter graphs
   unsigned* bar = nullptr;  // grid-barrier counter and error word of the persistent filter
+  void* ptab = nullptr;     // full phase table z D_s per vector (double-float persistent filter)
+  size_t ptab_bytes = 0;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 

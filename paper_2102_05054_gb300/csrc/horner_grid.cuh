@@ -41,6 +41,8 @@ template <typename Real> struct HornerGridArgs {
   const cplx<Real>* coef;    // GEN: c_j of vector v at coef[v * coef_stride + j], j = 1..k-1
   int64_t coef_stride;
   int64_t nsteps;            // k: step 0 plus k - 1 Horner updates
+  const cplx<Real>* ptab;    // nullable: the full phase table z D_s per vector (stride d),
+                             // replacing the product of the two chunk tables
   int psi_smem;              // psi_in of the CTA's two tiles kept in shared memory (one tile
                              // per CTA and layout: grid == tiles per layout)
   unsigned* bar;             // kBarWords words: [0] arrivals, [kBarErr] error (zero at launch)
@@ -137,7 +139,9 @@ __device__ __forceinline__ void transpose_tile(cplx<Real> (&v)[1 << RB], cplx<Re
 // the top mapping round_g(0) down to the last round's mapping; reverse (REV): from the last
 // round's mapping back up to the top one. Either way NT transposes and the same butterflies
 // (the single-qubit factors commute).
-template <typename Real, int NB, int RB, int KF, bool SWAP, bool REV>
+// NORM0: the values entering the first round are normalised double-floats (they come from the
+// epilogue), so that round skips the renormalisation.
+template <typename Real, int NB, int RB, int KF, bool SWAP, bool REV, bool NORM0 = false>
 __device__ __forceinline__ void kick_rounds(cplx<Real> (&v)[1 << RB], cplx<Real>* sm, int t,
                                             scal<Real> tau) {
   constexpr int NT = pipe_transposes(NB, RB, KF);
@@ -148,7 +152,10 @@ __device__ __forceinline__ void kick_rounds(cplx<Real> (&v)[1 << RB], cplx<Real>
     const int hi = i == 0 ? NB : round_g(NB, RB, i - 1);
     if (j > 0) transpose_tile<Real, RB>(v, sm, t, REV ? round_g(NB, RB, i + 1)
                                                       : round_g(NB, RB, i - 1), g);
-    kick_registers<Real, RB, SWAP>(v, g, KF, hi, tau);
+    if (NORM0 && j == 0)
+      kick_registers<Real, RB, SWAP, false>(v, g, KF, hi, tau);
+    else
+      kick_registers<Real, RB, SWAP, true>(v, g, KF, hi, tau);
   }
 }
 
@@ -233,7 +240,8 @@ __device__ __forceinline__ void horner_tile(const HornerGridArgs<Real>& A, cplx<
       for (int c = 0; c < CH; ++c) {
         const int r = r0 + c;
         const uint32_t s = tb + tile_to_global<NB, C, LAYB>((uint32_t)r << g_last);
-        const Cx p = zmul(__ldg(&tlo[s & lomask]), __ldg(&thi[((s >> am1) << 1) | (s & 1u)]));
+        const Cx p = A.ptab ? __ldg(&A.ptab[vec * A.d + s])
+                            : zmul(__ldg(&tlo[s & lomask]), __ldg(&thi[((s >> am1) << 1) | (s & 1u)]));
         const Cx base = GEN ? zmul(cj, pin[c]) : pin[c];
         v[r] = zfma(p, v[r], base);
       }
@@ -246,7 +254,7 @@ __device__ __forceinline__ void horner_tile(const HornerGridArgs<Real>& A, cplx<
       for (int r = 0; r < R; ++r) dst[tile_to_global<NB, C, LAYB>((uint32_t)r << g_last)] = v[r];
       return;
     }
-    kick_rounds<Real, NB, RB, KF, SWAP, true>(v, sm, t, A.tau);
+    kick_rounds<Real, NB, RB, KF, SWAP, true, true>(v, sm, t, A.tau);
   } else {
     kick_rounds<Real, NB, RB, KF, SWAP, false>(v, sm, t, A.tau);
     if (NT > 0) transpose_tile<Real, RB>(v, sm, t, g_last, g_top);

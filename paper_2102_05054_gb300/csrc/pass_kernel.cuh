@@ -168,10 +168,10 @@ template <int RB> __device__ __forceinline__ int tile_elem(int t, int r, int g) 
   return (t & ((1 << g) - 1)) | (r << g) | ((t >> g) << (g + RB));
 }
 
-template <typename Real, int RB, bool SWAP>
+template <typename Real, int RB, bool SWAP, bool RENORM = true>
 __device__ __forceinline__ void kick_registers(cplx<Real> (&v)[1 << RB], int g, int lo, int hi,
                                                scal<Real> tau) {
-  if constexpr (std::is_same<Real, dfloat>::value) {
+  if constexpr (std::is_same<Real, dfloat>::value && RENORM) {
     // renormalise the double-float pairs left unnormalised by the previous round
 #pragma unroll
     for (int r = 0; r < (1 << RB); ++r) v[r] = df_renorm(v[r]);

@@ -606,14 +606,14 @@ static int orth_block(Workspace& ws, double2* S, int64_t d, int n0, int nn, doub
 }
 
 // FP64 polish of the FILTER_FP32 result (one problem): the Ritz step with U on approximate
-// eigenvectors that the Sec. 4 footnote suggests, iterated on a growing search space until
-// the U-residuals reach tol_resid.
+// eigenvectors that the Sec. 4 footnote suggests, iterated until the U-residuals reach
+// tol_resid.
 //
 // Each iteration: Rayleigh-Ritz with U in complex128 on span(S) (G = S^H U S, its eigen-
 // decomposition on the device); the block = the nb Ritz pairs with the largest |g_k(omega)|
 // (values off the unit circle are mixtures and rank last); stop when the nev in-lobe pairs
-// closest to exp(i phi) have residual <= tol_resid. Otherwise extend S by a correction for
-// every selected pair still above tol_resid / 10: with r = (U - omega) x formed in FP64 and the
+// closest to exp(i phi) have residual <= tol_resid. Otherwise compute a correction for every
+// selected pair still above tol_resid / 10: with r = (U - omega) x formed in FP64 and the
 // filter g_K centred on omega itself,
 //     g_K(U / omega) x - K x = q(U) r,   q(U) = sum_{l < K-1} (K-1-l) omega^{-(l+1)} U^l,
 // (Sec. 3, Eq. geo, the defect of the geometric sum at its own peak), so q(U) r is
@@ -621,53 +621,83 @@ static int orth_block(Workspace& ws, double2* S, int64_t d, int n0, int nn, doub
 // come back multiplied by about -K, those near omega are suppressed. Only the small residual
 // r goes through the complex64 sweeps (Horner form with the coefficients K-1-l), so their
 // rounding is relative to ||r||. The corrections of all pairs share one batched filter
-// launch. K = k/4 by default (FLOQUET_POLISH_K sets it): a shorter filter resolves less per
-// correction, but the search space keeps every earlier correction, so the directions the
-// errors of different pairs share accumulate. When S would exceed its cap (the small
-// eigensolver's 512), it restarts from the block's Ritz vectors.
+// launch; K = k/2 by default (FLOQUET_POLISH_K sets it).
+// The next space is [Ritz block, the last kWindow correction blocks] (an LOBPCG-like window):
+// the earlier blocks carry what the previous corrections found, so the error components that
+// the pairs share keep converging while the space stays bounded. The Ritz block and the kept
+// blocks lie in span(S): they are re-based by a coefficient matrix (no new U applications);
+// only the new corrections need U in FP64.
 int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double tol_resid,
-           int max_iter, double2* X0, int nb, int64_t d, std::vector<cd>& omega_out,
+           int max_iter, double2* X0, int nb_in, int64_t d, std::vector<cd>& omega_out,
            std::vector<double>& resid_out, std::vector<int>& cols_out, int* iters,
            cudaStream_t st) {
   const bool verbose = getenv("FLOQUET_VERBOSE") != nullptr;
-  int64_t K = std::max<int64_t>(2, k / 4);
+  int64_t K = std::max<int64_t>(2, k / 2);
   if (const char* e = getenv("FLOQUET_POLISH_K")) K = std::max<int64_t>(2, atoll(e));
-  const int smax = std::min(512, std::max(3 * nb, nb + 64));
+  // block: the wanted pairs and guard directions (the largest |g_k| beyond them)
+  const int nb = std::min(nb_in, nev + std::max(16, nev / 4));
+  // correction blocks kept in the space (3, or fewer so that the space fits the small
+  // eigensolver's 512)
+  int kWindow = 3;
+  if (const char* e = getenv("FLOQUET_POLISH_WINDOW")) kWindow = std::max(1, atoi(e));
+  kWindow = std::min(kWindow, (512 - nb) / std::max(1, nb));
+  if (kWindow < 1) {
+    set_error("polish: nev %d too large for the Rayleigh-Ritz space", nev);
+    return FLOQUET_EINVAL;
+  }
+  const int smax = nb + kWindow * nb;
   const double drop = 1e-6;
-  DevBuf<double2> S, W, T, M, G, Yg, Ysel, lam, eigw, X, UX, R, Cv;
+  DevBuf<double2> S, W, S2, W2, T, M, G, Gt, Yg, Ysel, Mq, lam, eigw, X, UX, R, Cb;
   DevBuf<double> rq;
   DevBuf<int> info;
   DevBuf<float2> zs, hc;
+  DevBuf<float4> zsd, hcd;  // double-float copies for the later correction steps
   FQ_TRY(S.alloc((size_t)smax * d));
   FQ_TRY(W.alloc((size_t)smax * d));
+  FQ_TRY(S2.alloc((size_t)smax * d));
+  FQ_TRY(W2.alloc((size_t)smax * d));
   FQ_TRY(T.alloc((size_t)nb * d));
   FQ_TRY(M.alloc((size_t)smax * nb));
   FQ_TRY(G.alloc((size_t)smax * smax));
+  FQ_TRY(Gt.alloc((size_t)smax * smax));
   FQ_TRY(Yg.alloc((size_t)smax * smax));
   FQ_TRY(Ysel.alloc((size_t)smax * nb));
+  FQ_TRY(Mq.alloc((size_t)smax * smax));
   FQ_TRY(lam.alloc(smax));
   FQ_TRY(eigw.alloc(small_eig_work_elems(smax)));
   FQ_TRY(info.alloc(1));
   FQ_TRY(X.alloc((size_t)nb * d));
   FQ_TRY(UX.alloc((size_t)nb * d));
   FQ_TRY(R.alloc((size_t)nb * d));
+  FQ_TRY(Cb.alloc((size_t)nb * d));
   FQ_TRY(rq.alloc((size_t)3 * nb));
+  // the correction sweeps run in complex64; FLOQUET_POLISH_DF_FROM = i runs the steps from
+  // the i-th on in double-float instead
+  int df_from = 1 << 30;
+  if (const char* e = getenv("FLOQUET_POLISH_DF_FROM")) df_from = std::max(0, atoi(e));
   FQ_TRY(zs.alloc(nb));
   FQ_TRY(hc.alloc((size_t)K));
+  FQ_TRY(zsd.alloc(nb));
+  FQ_TRY(hcd.alloc((size_t)K));
   {  // Horner coefficients of q: hc[j] = j + 1 (hc[0] unused)
     std::vector<float2> h((size_t)K);
-    for (int64_t j = 0; j < K; ++j) h[j] = make_float2((float)(j + 1), 0.0f);
+    std::vector<float4> hd((size_t)K);
+    for (int64_t j = 0; j < K; ++j) {
+      h[j] = make_float2((float)(j + 1), 0.0f);
+      hd[j] = from_d2<dfloat>(make_double2((double)(j + 1), 0.0));
+    }
     FQ_CUDA(cudaMemcpyAsync(hc.p, h.data(), sizeof(float2) * K, cudaMemcpyHostToDevice, st));
+    FQ_CUDA(cudaMemcpyAsync(hcd.p, hd.data(), sizeof(float4) * K, cudaMemcpyHostToDevice, st));
+    FQ_CUDA(cudaStreamSynchronize(st));
   }
-  // initial space: the converged Ritz block
+  // initial space: the block of the converged Ritz vectors with the largest |theta|
   FQ_CUDA(cudaMemcpyAsync(S.p, X0, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
   int ns = 0;
   FQ_TRY(orth_block(ws, S.p, d, 0, nb, drop, T.p, M.p, &ns, st));
-  auto rebuild = [&]() -> int {  // W = U S, G = S^H W
-    FQ_TRY(apply_u<double>(op, S.p, W.p, ns, ns, st));
-    return gemm_cn(ws, S.p, d, 0, W.p, d, 0, d, ns, ns, 1, G.p, smax, 0, st);
-  };
-  FQ_TRY(rebuild());
+  FQ_TRY(apply_u<double>(op, S.p, W.p, ns, ns, st));
+  FQ_TRY(gemm_cn(ws, S.p, d, 0, W.p, d, 0, d, ns, ns, 1, G.p, smax, 0, st));
+  // column ranges of S holding the kept correction blocks, oldest first
+  std::vector<std::pair<int, int>> blocks;
   std::vector<double2> lam_h(smax);
   std::vector<double> rq_h(3 * nb);
   int corrections = 0;
@@ -697,7 +727,9 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
       FQ_CUDA(cudaMemcpyAsync(Ysel.p + (size_t)i * ns, Yg.p + (size_t)order[i] * ns,
                               sizeof(double2) * ns, cudaMemcpyDeviceToDevice, st));
     FQ_TRY(gemm_nn(S.p, d, 0, Ysel.p, ns, 0, X.p, d, 0, d, ns, nk, 1, st));
-    FQ_TRY(gemm_nn(W.p, d, 0, Ysel.p, ns, 0, UX.p, d, 0, d, ns, nk, 1, st));
+    // U X by a fresh FP64 application (not W Y): the residuals do not depend on how
+    // accurately the re-based W still equals U S
+    FQ_TRY(apply_u<double>(op, X.p, UX.p, nk, nk, st));
     FQ_TRY(rayleigh_residual(ws, X.p, UX.p, d, nk, rq.p, st));
     FQ_CUDA(cudaMemcpyAsync(rq_h.data(), rq.p, sizeof(double) * 3 * nk, cudaMemcpyDeviceToHost,
                             st));
@@ -720,17 +752,12 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
       resid_out.push_back(rq_h[3 * i + 2]);
     }
     *iters = it;
-    // pairs to correct: the selected pairs (or, while fewer than nev are candidates, the
-    // whole block) still above a tenth of the target, worst first
+    // pairs to correct: every block member still above a tenth of the target, the guard
+    // directions included (a guard left unconverged would mix back into the nearly degenerate
+    // wanted pairs at the next Rayleigh-Ritz step)
     std::vector<int> act;
-    if (sel.size() < (size_t)nev) {
-      for (int i = 0; i < nk; ++i)
-        if (rq_h[3 * i + 2] > 0.1 * tol_resid) act.push_back(i);
-    } else {
-      for (int i : sel)
-        if (rq_h[3 * i + 2] > 0.1 * tol_resid) act.push_back(i);
-    }
-    std::sort(act.begin(), act.end(), [&](int a, int b) { return rq_h[3 * a + 2] > rq_h[3 * b + 2]; });
+    for (int i = 0; i < nk; ++i)
+      if (rq_h[3 * i + 2] > 0.1 * tol_resid) act.push_back(i);
     const int nf = (int)act.size();
     if (verbose)
       fprintf(stderr, "floquet polish: iter %d space %d block %d worst selected resid %.3e "
@@ -743,30 +770,96 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
     // residual vectors of the pairs to correct, then q(U) r in one batched filter launch
     FQ_TRY(residual_vectors(X.p, UX.p, R.p, d, nk, rq.p, st));
     for (int j = 0; j < nf; ++j)
-      if (act[j] != j)
-        FQ_CUDA(cudaMemcpyAsync(T.p + (size_t)j * d, R.p + (size_t)act[j] * d,
-                                sizeof(double2) * d, cudaMemcpyDeviceToDevice, st));
-      else
-        FQ_CUDA(cudaMemcpyAsync(T.p + (size_t)j * d, R.p + (size_t)j * d, sizeof(double2) * d,
-                                cudaMemcpyDeviceToDevice, st));
+      FQ_CUDA(cudaMemcpyAsync(T.p + (size_t)j * d, R.p + (size_t)act[j] * d,
+                              sizeof(double2) * d, cudaMemcpyDeviceToDevice, st));
     std::vector<float2> zh(nf);
+    std::vector<float4> zhd(nf);
     for (int j = 0; j < nf; ++j) {
       const cd z = 1.0 / om[act[j]];
       zh[j] = make_float2((float)z.real(), (float)z.imag());
+      zhd[j] = from_d2<dfloat>(make_double2(z.real(), z.imag()));
     }
-    FQ_CUDA(cudaMemcpyAsync(zs.p, zh.data(), sizeof(float2) * nf, cudaMemcpyHostToDevice, st));
-    // restart the space from the block when the corrections would not fit
-    if (ns + nf > smax) {
-      FQ_CUDA(cudaMemcpyAsync(S.p, X.p, sizeof(double2) * nk * d, cudaMemcpyDeviceToDevice,
+    if (it >= df_from) {
+      FQ_CUDA(cudaMemcpyAsync(zsd.p, zhd.data(), sizeof(float4) * nf, cudaMemcpyHostToDevice,
                               st));
-      FQ_TRY(orth_block(ws, S.p, d, 0, nk, drop, R.p, M.p, &ns, st));
-      FQ_TRY(rebuild());
+      FQ_CUDA(cudaStreamSynchronize(st));
+      FQ_TRY((filter_horner_coef<dfloat, double>(op, T.p, d, Cb.p, d, zsd.p, hcd.p, K - 1, nf,
+                                                 st)));
+    } else {
+      FQ_CUDA(cudaMemcpyAsync(zs.p, zh.data(), sizeof(float2) * nf, cudaMemcpyHostToDevice,
+                              st));
+      FQ_CUDA(cudaStreamSynchronize(st));
+      FQ_TRY((filter_horner_coef<float, double>(op, T.p, d, Cb.p, d, zs.p, hc.p, K - 1, nf,
+                                                st)));
     }
-    double2* Cdst = S.p + (size_t)ns * d;
-    FQ_TRY((filter_horner_coef<float, double>(op, T.p, d, Cdst, d, zs.p, hc.p, K - 1, nf, st)));
     corrections += nf;
+    // re-base the kept part of the space, [Ritz block, the newest kWindow - 1 correction
+    // blocks] = S Z, by an orthonormal coefficient matrix Mq spanning the columns of Z in that
+    // order (Gram-Schmidt twice on the host; a column whose remaining length is below 1e-8 is
+    // dropped), so that each kept block's remainder stays a contiguous range of columns
+    {
+      while ((int)blocks.size() > kWindow - 1) blocks.erase(blocks.begin());
+      int nz = nk;
+      for (auto& b : blocks) nz += b.second;
+      std::vector<double2> yh((size_t)ns * nk);
+      FQ_CUDA(cudaMemcpyAsync(yh.data(), Ysel.p, sizeof(double2) * ns * nk,
+                              cudaMemcpyDeviceToHost, st));
+      FQ_CUDA(cudaStreamSynchronize(st));
+      std::vector<cd> q((size_t)ns * nz);
+      int nq = 0;
+      std::vector<cd> col(ns);
+      std::vector<std::pair<int, int>> nblocks;
+      int c = 0;
+      for (int g = -1; g < (int)blocks.size(); ++g) {
+        const int gcols = g < 0 ? nk : blocks[g].second;
+        const int start = nq;
+        for (int cc = 0; cc < gcols; ++cc, ++c) {
+          for (int r = 0; r < ns; ++r)
+            col[r] = g < 0 ? cd(yh[(size_t)cc * ns + r].x, yh[(size_t)cc * ns + r].y)
+                           : (r == blocks[g].first + cc ? cd(1.0, 0.0) : cd(0.0, 0.0));
+          double n0 = 0;
+          for (int r = 0; r < ns; ++r) n0 += std::norm(col[r]);
+          n0 = std::sqrt(n0);
+          if (!(n0 > 0)) continue;
+          for (int pass = 0; pass < 2; ++pass)
+            for (int j2 = 0; j2 < nq; ++j2) {
+              const cd* qj = &q[(size_t)j2 * ns];
+              cd h = 0;
+              for (int r = 0; r < ns; ++r) h += std::conj(qj[r]) * col[r];
+              for (int r = 0; r < ns; ++r) col[r] -= h * qj[r];
+            }
+          double n1 = 0;
+          for (int r = 0; r < ns; ++r) n1 += std::norm(col[r]);
+          n1 = std::sqrt(n1);
+          if (!(n1 > 1e-8 * n0)) continue;
+          for (int r = 0; r < ns; ++r) q[(size_t)nq * ns + r] = col[r] / n1;
+          ++nq;
+        }
+        if (g >= 0 && nq > start) nblocks.push_back({start, nq - start});
+      }
+      blocks = nblocks;
+      std::vector<double2> mq((size_t)ns * nq);
+      for (size_t t = 0; t < mq.size(); ++t) mq[t] = make_double2(q[t].real(), q[t].imag());
+      FQ_CUDA(cudaMemcpyAsync(Mq.p, mq.data(), sizeof(double2) * ns * nq,
+                              cudaMemcpyHostToDevice, st));
+      FQ_TRY(gemm_nn(S.p, d, 0, Mq.p, ns, 0, S2.p, d, 0, d, ns, nq, 1, st));
+      FQ_TRY(gemm_nn(W.p, d, 0, Mq.p, ns, 0, W2.p, d, 0, d, ns, nq, 1, st));
+      // G <- Mq^H G Mq
+      FQ_TRY(small_gemm_batched('N', 'N', ns, nq, ns, G.p, smax, 0, Mq.p, ns, 0, Gt.p, smax, 0,
+                                1, st));
+      FQ_TRY(small_gemm_batched('C', 'N', nq, nq, ns, Mq.p, ns, 0, Gt.p, smax, 0, G.p, smax, 0,
+                                1, st));
+      std::swap(S.p, S2.p);
+      std::swap(W.p, W2.p);
+      ns = nq;
+    }
+    // append the new corrections, orthonormalised against the re-based space
+    double2* Cdst = S.p + (size_t)ns * d;
+    FQ_CUDA(cudaMemcpyAsync(Cdst, Cb.p, sizeof(double2) * nf * d, cudaMemcpyDeviceToDevice,
+                            st));
     int nc = 0;
     FQ_TRY(orth_block(ws, S.p, d, ns, nf, drop, T.p, M.p, &nc, st));
+    if (nc > 0) blocks.push_back({ns, nc});
     if (nc > 0) {
       FQ_TRY(apply_u<double>(op, Cdst, W.p + (size_t)ns * d, nc, nc, st));
       // G[:ns, ns:ns+nc] = S_old^H W_new; G[ns:ns+nc, :ns+nc] = S_new^H W

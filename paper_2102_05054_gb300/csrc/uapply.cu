@@ -404,6 +404,7 @@ void op_free(floquet_op* op) {
   cudaFree(op->zlo);
   cudaFree(op->coef);
   cudaFree(op->bar);
+  cudaFree(op->ptab);
 }
 
 template <typename Real> static const Plan& plan_of(const floquet_op* op);
@@ -455,6 +456,57 @@ static int u_passes(floquet_op* op, const cplx<Real>* in, cplx<Real>* out, int n
 }
 
 static void destroy_graphs(floquet_op* op);
+
+// out[v * d + s] = zs[v] * D_s (times the kick scale; zs null: z = 1), the product of the two
+// chunk tables formed in float64, for the persistent kernel's full phase table
+template <typename Real>
+__global__ void phase_table_kernel(const double2* __restrict__ tlo, const double2* __restrict__ thi,
+                                   int a, int vpp, int64_t lo_n, int64_t hi_n,
+                                   const cplx<Real>* __restrict__ zs, cplx<Real>* __restrict__ out,
+                                   int64_t d) {
+  const int64_t v = blockIdx.y;
+  const int64_t prob = v / vpp;
+  const double2 z = zs ? to_d2(zs[v]) : make_double2(1.0, 0.0);
+  const uint32_t lomask = (1u << a) - 1u;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < d;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t u = (uint32_t)s;
+    const double2 p = cmul(tlo[prob * lo_n + (u & lomask)],
+                           thi[prob * hi_n + (((u >> (a - 1)) << 1) | (u & 1u))]);
+    out[v * d + s] = from_d2<Real>(cmul(z, p));
+  }
+}
+
+// The persistent kernel's full phase table for double-float sweeps with up to 2^23 table
+// entries (*out stays null otherwise, and for the other precisions, whose sweeps are bound by
+// data movement rather than arithmetic).
+template <typename Real>
+static int build_phase_table(floquet_op* op, const cplx<Real>* zs, int nvec, int vpp,
+                             cudaStream_t st, const cplx<Real>** out) {
+  *out = nullptr;
+  const int64_t d = op->d;
+  if (!std::is_same<Real, dfloat>::value || (int64_t)nvec * d > (int64_t(1) << 23))
+    return FLOQUET_OK;
+  const size_t pbytes = (size_t)nvec * d * sizeof(cplx<Real>);
+  if (op->ptab_bytes < pbytes) {
+    cudaFree(op->ptab);
+    op->ptab = nullptr;
+    op->ptab_bytes = 0;
+    if (cudaMalloc(&op->ptab, pbytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("filter workspace: cudaMalloc of %zu bytes failed", pbytes);
+      return FLOQUET_ENOMEM;
+    }
+    op->ptab_bytes = pbytes;
+  }
+  phase_table_kernel<Real><<<dim3(grid_for(d, 256), nvec), 256, 0, st>>>(
+      op->tabs.lo64, op->tabs.hi64, op->tabs.a, vpp, op->tabs.lo_n, op->tabs.hi_n, zs,
+      reinterpret_cast<cplx<Real>*>(op->ptab), d);
+  count_launch();
+  FQ_CHECK_LAUNCH();
+  *out = reinterpret_cast<const cplx<Real>*>(op->ptab);
+  return FLOQUET_OK;
+}
 
 // Live test data for the autotuner: a normalised state with varied amplitudes.
 template <typename Real>
@@ -572,8 +624,8 @@ template <typename Real> static int tune(floquet_op* op, int nvec, cudaStream_t 
   if (!forced) set_variant<Real>(op, bestv);
   if (has_grid && !grid_forced && rc == FLOQUET_OK) {
     rc = ensure_bar(op);
-    const HornerGridArgs<Real> ga =
-        grid_args<Real>(op, pin, acc, tlo_of<Real>(op), 0, 11, nt, nt);
+    HornerGridArgs<Real> ga = grid_args<Real>(op, pin, acc, tlo_of<Real>(op), 0, 11, nt, nt);
+    if (rc == FLOQUET_OK) rc = build_phase_table<Real>(op, nullptr, nt, nt, st, &ga.ptab);
     float gbest = 3.0e38f;
     int gi = -1;
     for (int i = 0; i < (int)gs.size() && rc == FLOQUET_OK; ++i) {
@@ -868,8 +920,10 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
       FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, nullptr, pin, nullptr, 0, d, nvec,
                                             st)));
       FQ_TRY(ensure_bar(op));
-      const HornerGridArgs<Real> ga =
-          grid_args<Real>(op, pin, acc, zlo, lo_n, k, nvec, vec_per_prob);
+      HornerGridArgs<Real> ga = grid_args<Real>(op, pin, acc, zlo, lo_n, k, nvec, vec_per_prob);
+      // double-float: one table entry per amplitude (z D_s formed in float64) replaces the
+      // double-float product of the two chunk tables in every step (arithmetic bound sweep)
+      FQ_TRY(build_phase_table<Real>(op, zs, nvec, vec_per_prob, st, &ga.ptab));
       auto gbody = [&](cudaStream_t s) -> int { return gl(ga, op->swap, false, s); };
       FQ_TRY(run_loop(op, false, k, nvec, sweep_dtype<Real>(), FLOQUET_FORM_HORNER, zs,
                       vec_per_prob, 1, st, gbody));
