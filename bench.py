@@ -1,14 +1,17 @@
 """Benchmark: time to the nev eigenpairs closest to exp(i phi) of the L = 20 kicked-Ising
-Floquet operator (residual <= 1e-10), with the filter's U-application throughput against
-the HBM roofline.
+Floquet operator (every residual <= 1e-10), with the filter's U-application throughput
+against its roofline.
 
-One step = one complete solve of the workload through the C ABI: operator set-up, the
-Krylov-Schur Arnoldi on g_k(U) (filter sweeps, CGS2, small solve, restarts), Ritz vectors,
-Rayleigh quotients and residuals, and (FILTER_FP32 form) the FP64 polish. Inputs are
-synthetic: h_i ~ U[-1, 1] from a seeded generator, complex-Gaussian start vector.
+One step = one eigenproblem of the workload: a disorder realisation of its own (h_i ~ U[-1, 1],
+seeded), solved through the C ABI from the start vector to the nev pairs -- operator set-up,
+the Krylov-Schur Arnoldi on g_k(U) (filter sweeps, CGS2, small solves), Ritz vectors,
+Rayleigh quotients and FP64 residuals. Steps run --batch at a time in one lockstep solve
+(arnoldi_eigs_batched: the filter sweeps of the batch share each launch), so `value` is the
+solve time per eigenproblem at that batch size; a single problem's latency is the batch's
+solve time (reported as `latency_s`). Inputs are synthetic.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-N > 1 runs independent replicas (one disorder realisation per rank; no data-path
+N > 1 runs independent replicas (realisations of their own per rank; no data-path
 collective), launched with torch.distributed.run.
 """
 
@@ -125,6 +128,22 @@ def replica_seed(base_seed, rank):
     return base_seed + rank
 
 
+def step_seeds(base_seed, rank, steps):
+    """Disorder seeds of the K steps of one rank: realisation i of rank r uses
+    replica_seed(base_seed, r * K + i), so no two steps or ranks solve the same problem."""
+    return [replica_seed(base_seed, rank * steps + i) for i in range(steps)]
+
+
+def batches(steps, batch):
+    """Sizes of the lockstep solves that cover `steps` problems, `batch` at a time."""
+    out = []
+    left = steps
+    while left > 0:
+        out.append(min(batch, left))
+        left -= out[-1]
+    return out
+
+
 def max_over_ranks(value, device):
     """Max of a per-rank float over the process group (the job's time is its slowest rank)."""
     import torch
@@ -139,8 +158,7 @@ def max_over_ranks(value, device):
 def _cfg(args):
     from paper_2102_05054_gb300 import inputs
     c = dict(inputs.WORKLOADS[args.workload])
-    if args.precision:
-        c["precision"] = args.precision
+    c["precision"] = args.precision
     return c
 
 
@@ -157,77 +175,76 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     cfg = _cfg(args)
     L, k, m, nev, phi = cfg["L"], cfg["k"], cfg["m"], cfg["nev"], cfg["phi"]
-    prec = {"filter_fp32": floquet.FILTER_FP32, "fp64": floquet.FP64,
-            "filter_df": floquet.FILTER_DF}[cfg["precision"]]
+    prec = {"fp64": floquet.FP64, "filter_df": floquet.FILTER_DF}[cfg["precision"]]
     d = 1 << L
-    h = inputs.disorder(L, cfg["W"], replica_seed(cfg["seed"], rank))  # one per replica
-    v0_host = inputs.start_vector(L)
-    v0 = torch.from_numpy(v0_host).to(dev)
-    evecs = torch.empty((nev, d), dtype=torch.complex128, device=dev)
+    seeds = step_seeds(cfg["seed"], rank, args.steps)
+    hs = np.stack([inputs.disorder(L, cfg["W"], s) for s in seeds])  # one realisation per step
+    v0_pinned = torch.from_numpy(inputs.start_vector(L)).pin_memory()
+    v0 = torch.empty(d, dtype=torch.complex128, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
-
-    def one_solve(v0_arg, evecs_arg):
-        with floquet.Floquet(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h) as fq:
-            return fq.arnoldi_eigs(phi, k, nev, m, v0_arg, precision=prec,
-                                   max_restarts=args.max_restarts, evecs=evecs_arg)
+    phis = np.array([phi])
 
     def barrier():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # Warm-up. The last warm-up step is the end-to-end measurement: the public C-ABI call
-    # with HOST buffers (h and v0 in; eigenvalues, residuals and eigenvectors out), so the
-    # host<->device copies are inside its timed region.
-    evecs_host = np.empty((nev, d), dtype=np.complex128)
-    t_e2e, e2e_res = None, None
+    # Warm-up: no solves. Each warm-up builds an operator of the workload and runs a short
+    # filter with the batch width and sweep precision of the timed solves (module load, kernel
+    # images, the launch-shape autotuner's code paths, CUDA graph machinery).
+    sweep = {floquet.FP64: floquet.C128, floquet.FILTER_DF: floquet.C128_DF}[prec]
+    nb0 = batches(args.steps, args.batch)[0] if args.steps > 0 else args.batch
     for w in range(args.warmup):
-        flush.fill_(1.0)
+        with floquet.Floquet(L, inputs.J_DEFAULT, inputs.G_DEFAULT, hs[0]) as fq:
+            x = torch.zeros((nb0, d), dtype=torch.complex128, device=dev)
+            x[:, 0] = 1.0
+            y = torch.empty_like(x)
+            fq.filter_apply(phi, 9, x, y, form=floquet.FORM_HORNER, sweep=sweep)
         barrier()
-        if w == args.warmup - 1:
-            te = time.perf_counter()
-            e2e_res = one_solve(v0_host, evecs_host)
-            barrier()
-            t_e2e = time.perf_counter() - te
-        else:
-            one_solve(v0, evecs)
 
     sampler = ClockSampler(local)
     sampler.start()
     floquet.profile_enable(True)
     floquet.reset_launch_count()
-    times = []
-    results = None
-    for _ in range(args.steps):
+    dev_s, wall_s, lat = [], [], []
+    results = []
+    i0 = 0
+    for nb in batches(args.steps, args.batch):
+        hb = hs[i0:i0 + nb]
         flush.fill_(1.0)
         barrier()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        results = one_solve(v0, evecs)
-        t1.record(stream)
-        barrier()
-        times.append(t0.elapsed_time(t1) / 1000.0)
+        # e2e: the step's inputs from pinned host memory, the public C-ABI call, results on the
+        # host; value: the device time of the same call, inputs already resident
+        t0 = time.perf_counter()
+        v0.copy_(v0_pinned, non_blocking=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        om, res, nconv, rc = floquet.arnoldi_eigs_batched(
+            L, inputs.J_DEFAULT, inputs.G_DEFAULT, hb, phis, k, nev, m, v0,
+            tol=args.tol, precision=prec, max_restarts=args.max_restarts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        dev_s.append(e0.elapsed_time(e1) / 1000.0)
+        wall_s.append(t1 - t0)
+        lat.append(dev_s[-1])
+        results.append((om, res, nconv, rc, nb))
+        i0 += nb
     launches = floquet.launch_count()
     prof = floquet.profile_read()
     floquet.profile_enable(False)
     clocks = sampler.stop()
 
-    t_step = max_over_ranks(sum(times) / len(times), dev)
-    if t_e2e is None:  # no warm-up: measure the end-to-end call now
-        barrier()
-        te = time.perf_counter()
-        e2e_res = one_solve(v0_host, evecs_host)
-        barrier()
-        t_e2e = time.perf_counter() - te
-    om_e, res_e, nconv_e, rc_e = e2e_res
-
-    om, res, nconv, rc = results
-    kind = {floquet.FILTER_FP32: "c64", floquet.FP64: "c128", floquet.FILTER_DF: "df"}[prec]
+    t_step = max_over_ranks(sum(dev_s) / args.steps, dev)
+    t_e2e = max_over_ranks(sum(wall_s) / args.steps, dev)
+    kind = {floquet.FP64: "c128", floquet.FILTER_DF: "df"}[prec]
     sweep_ms, u_apps, alg_bytes = prof[kind]
+    max_res = max(float(np.max(r[1])) for r in results)
+    n_conv = int(sum(int(np.sum(r[2])) for r in results))
+    status = [int(r[3]) for r in results]
     hbm, peak_kind = _peaks()
-    form = os.environ.get("FLOQUET_KRYLOV_FORM", "horner")
     out = None
     if rank == 0:
         achieved = alg_bytes / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
@@ -243,45 +260,48 @@ def run_gpu(args):
             # the double-float sweep is bound by the FP32 pipe: algorithmic FP32 instructions
             # per U application against the FP32 issue rate at the maximum clock
             peak_t, mhz = _fp32_peak_tops()
-            ipa = df_instr_per_amplitude(L, form)
+            ipa = df_instr_per_amplitude(L, "horner")
             ach_t = ipa * d * u_apps / (sweep_ms / 1e3) / 1e12
             roofline = {"bound": "alu", "achieved": round(ach_t, 2), "peak": round(peak_t, 2),
                         "unit": "T FP32 instr/s", "frac": round(ach_t / peak_t, 4),
-                        "traffic": traffic, "kernel": "U application (pass_pipe_kernel x2)",
+                        "traffic": traffic,
+                        "kernel": "U application (double-float pass kernels, Horner filter)",
                         "fp32_instr_per_amplitude": ipa, "u_applications": int(u_apps),
                         "sweep_s": round(sweep_ms / 1e3, 3),
                         "peak_source": f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x "
                                        f"{mhz:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)",
                         "hbm_view": hbm_view}
         else:
-            roofline = dict(hbm_view, kernel="U application (pass kernels)",
+            roofline = dict(hbm_view, kernel="U application (Horner filter)",
                             u_applications=int(u_apps), sweep_s=round(sweep_ms / 1e3, 3))
+        h2d = int(d * 16 + L * 8)  # start vector and the step's field h, per step
+        d2h = int(nev * 24 + 4)   # eigenvalues, residuals and n_conv, per step
         out = {
             "metric": METRIC, "value": round(t_step, 4), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 2),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"c64": "c64 sweeps / f64 Arnoldi", "c128": "c128 / f64",
-                      "df": "double-float (2 x f32) sweeps / f64 Arnoldi"}[kind],
-            "data": "synthetic (seeded h_i ~ U[-1,1], complex-Gaussian start vector)",
+            "dtype": {"df": "double-float (2 x f32) sweeps / f64 Arnoldi",
+                      "c128": "c128 sweeps / f64 Arnoldi"}[kind],
+            "data": "synthetic (seeded h_i ~ U[-1,1], one realisation per step; complex-"
+                    "Gaussian start vector)",
             "config": {"workload": args.workload, "L": L, "J": inputs.J_DEFAULT,
                        "g": inputs.G_DEFAULT, "W": cfg["W"], "phi": phi, "k": k, "m": m,
-                       "nev": nev, "precision": cfg["precision"],
-                       "filter_form": os.environ.get("FLOQUET_KRYLOV_FORM", "horner"),
+                       "nev": nev, "precision": cfg["precision"], "filter_form": "horner",
+                       "batch": args.batch, "krylov_tol": args.tol,
                        "parallelism": f"replicas x{ws}",
-                       "l2": "working set larger than L2 (Krylov basis 4 GiB) and a 256 MiB "
-                             "buffer written between steps"},
-            "result": {"status": rc, "n_conv": nconv, "max_resid": float(np.max(res)),
-                       "omega_first": [float(om[0].real), float(om[0].imag)]},
-            "e2e": {"value": round(t_e2e, 4), "unit": UNIT,
-                    "h2d_bytes_per_step": int(d * 16 + L * 8),
-                    "d2h_bytes_per_step": int(nev * d * 16 + nev * 24),
-                    "status": rc_e, "n_conv": nconv_e},
+                       "l2": "working set larger than L2 (Krylov bases 4 GiB per problem) and "
+                             "a 256 MiB buffer written before every batch"},
+            "latency_s": round(max(lat), 3),
+            "result": {"status": status, "n_conv": n_conv, "problems": args.steps,
+                       "max_resid": max_res},
+            "e2e": {"value": round(t_e2e, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
             "roofline": roofline,
             "gpu_launches": int(launches // max(1, args.steps)),
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(cfg, u_apps // max(1, args.steps), h,
+            out["cpu_baseline"] = cpu_baseline(cfg, u_apps // max(1, args.steps), hs[0],
                                                seconds=args.cpu_seconds)
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -291,48 +311,71 @@ def run_gpu(args):
 
 
 # Kernels whose committed ncu counters were taken on the current code (others report null).
-_CURRENT_TRAFFIC = {"df"}
+_CURRENT_TRAFFIC = set()
 
 
 def _ncu_traffic(L, kind):
     """DRAM bytes per U application from the committed ncu summary, if one matches the
     current kernel."""
-    name = "pass_pipe_kernel" if kind == "df" else "pass_kernel"
-    p = os.path.join(ROOT, "profiles", f"{name}_L{L}_{kind}_traffic.json")
+    p = os.path.join(ROOT, "profiles", f"pass_pipe_kernel_L{L}_{kind}_traffic.json")
     if kind in _CURRENT_TRAFFIC and os.path.exists(p):
         with open(p) as f:
             return json.load(f).get("dram_bytes_per_u_application")
     return None
 
 
-def cpu_baseline(cfg, u_apps_per_solve, h, seconds=15.0):
-    """The oracle as it stands on the host cores: time oracle U applications at the
-    workload's L for ~`seconds`, then scale to the U applications one GPU solve performed
-    (the filter sweeps dominate the solve; CGS2 and the small solves are not counted, so the
-    CPU figure is a lower bound)."""
+def _oracle_worker(args):
+    """One host process: oracle U applications at L for about `seconds` (numpy, one BLAS
+    thread); returns (applications, elapsed)."""
+    L, h, seconds, seed = args
+    os.environ["OMP_NUM_THREADS"] = "1"
+    sys.path.insert(0, ROOT)
     from oracle import model
 
     from paper_2102_05054_gb300 import inputs
-    L = cfg["L"]
     op = model.KickedIsing(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h)
-    psi = inputs.complex_gaussian(1 << L, 1)
+    psi = inputs.complex_gaussian(1 << L, seed)
     n = 0
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds or n < 2:
+    while time.perf_counter() - t0 < seconds or n < 1:
         psi = op.apply_u(psi)
         n += 1
-    dt = (time.perf_counter() - t0) / n
-    total = dt * u_apps_per_solve
-    return {"value": round(total, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} oracle U applications at L={L} ({dt:.3f} s each, numpy, one "
-                      f"thread) scaled to the {u_apps_per_solve} U applications of one GPU "
-                      f"solve; host has {os.cpu_count()} cores"}
+    return n, time.perf_counter() - t0
+
+
+def oracle_throughput(L, h, seconds, workers):
+    """U applications per second of the oracle on `workers` host processes, each applying U
+    to an independent vector (a spawn pool: safe after the GPU is in use)."""
+    import multiprocessing as mp
+    if workers <= 1:
+        n, dt = _oracle_worker((L, h, seconds, 7))
+        return n / dt, 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        res = pool.map(_oracle_worker, [(L, h, seconds, 7 + i) for i in range(workers)])
+    return sum(n / dt for n, dt in res), workers
+
+
+def cpu_baseline(cfg, u_apps_per_solve, h, seconds=10.0):
+    """The oracle as it stands on the host cores: oracle U applications at the workload's L,
+    one process per core on independent vectors for ~`seconds`, projected to the U
+    applications of one GPU solve (the filter sweeps dominate the solve; CGS2 and the small
+    solves are not counted, so the CPU figure is a lower bound)."""
+    L = cfg["L"]
+    workers = os.cpu_count() or 1
+    rate, used = oracle_throughput(L, h, seconds, workers)
+    total = u_apps_per_solve / rate
+    return {"value": round(total, 1), "unit": UNIT, "cores": used, "kind": "oracle",
+            "projected": True,
+            "sample": f"oracle U applications at L={L} (numpy, {used} processes x 1 BLAS "
+                      f"thread, ~{seconds:.0f} s each): {rate:.2f} applications/s in total, "
+                      f"projected to the {u_apps_per_solve} U applications of one GPU solve; "
+                      f"host has {os.cpu_count()} cores"}
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle on this machine's host cores, bounded sample per step."""
-    from oracle import model
-
+    """--impl reference: the CPU oracle on this machine's host cores, bounded sample per step,
+    projected to one solve."""
     from paper_2102_05054_gb300 import inputs
     ws, rank, _ = _dist()
     if rank != 0:
@@ -340,50 +383,96 @@ def run_reference(args):
     cfg = _cfg(args)
     L, k, m = cfg["L"], cfg["k"], cfg["m"]
     h = inputs.disorder(L, cfg["W"], cfg["seed"])
-    op = model.KickedIsing(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h)
     # U applications of one solve: at least m filters of k - 1 applications (one Krylov build)
     u_apps = m * (k - 1)
-    psi = inputs.complex_gaussian(1 << L, 1)
+    workers = os.cpu_count() or 1
     vals = []
     for step in range(args.warmup + args.steps):
-        n = 0
-        t0 = time.perf_counter()
-        while time.perf_counter() - t0 < args.ref_seconds or n < 1:
-            psi = op.apply_u(psi)
-            n += 1
+        rate, used = oracle_throughput(L, h, args.ref_seconds, workers)
         if step >= args.warmup:
-            vals.append((time.perf_counter() - t0) / n * u_apps)
+            vals.append(u_apps / rate)
     v = sum(vals) / len(vals)
+    sample = (f"oracle U applications for ~{args.ref_seconds} s per step on {used} host "
+              f"processes (one BLAS thread each), projected to m*(k-1) = {u_apps} "
+              f"applications (one Krylov build); host has {os.cpu_count()} cores")
     out = {"metric": METRIC, "value": round(v, 1), "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded h_i ~ U[-1,1])", "impl": "reference",
            "config": {"workload": args.workload, "L": L, "k": k, "m": m, "nev": cfg["nev"],
                       "parallelism": "host cores"},
-           "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"oracle U applications for ~{args.ref_seconds} s per "
-                                      f"step, scaled to m*(k-1) = {u_apps} applications "
-                                      f"(one Krylov build); host has {os.cpu_count()} cores"},
+           "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": used, "kind": "oracle",
+                            "projected": True, "sample": sample},
            "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return out
 
 
+def u_timing(Ls, nvecs=(1, 2, 4), k=513, reps=3):
+    """Per-U-application time of the Horner filter (k terms, CUDA events on the launching
+    stream, after two warm-up filters) for each sweep precision, state count and L: one JSON
+    line per case. The filter runs whatever launch shape the autotuner picked for the
+    operator (FLOQUET_VERBOSE=1 prints the tuner's timings)."""
+    import torch
+
+    from paper_2102_05054_gb300 import floquet, inputs
+    names = {floquet.C64: "c64", floquet.C128_DF: "df", floquet.C128: "c128"}
+    for L in Ls:
+        d = 1 << L
+        h = inputs.disorder(L, 1.0, 1)
+        for sweep in (floquet.C64, floquet.C128_DF, floquet.C128):
+            for nvec in nvecs:
+                if sweep == floquet.C128 and nvec > 1:
+                    continue
+                dt = torch.complex64 if sweep == floquet.C64 else torch.complex128
+                with floquet.Floquet(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h) as fq:
+                    x = torch.from_numpy(inputs.random_states(d, nvec, 3).T.copy()).to(dt).cuda()
+                    y = torch.empty_like(x)
+                    stream = torch.cuda.current_stream()
+                    for _ in range(2):
+                        fq.filter_apply(0.0, k, x, y, form=floquet.FORM_HORNER, sweep=sweep)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(reps):
+                        fq.filter_apply(0.0, k, x, y, form=floquet.FORM_HORNER, sweep=sweep)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    us = 1000.0 * e0.elapsed_time(e1) / (reps * (k - 1) * nvec)
+                b = 8 if sweep == floquet.C64 else 16
+                print(json.dumps({"L": L, "sweep": names[sweep], "nvec": nvec, "k": k,
+                                  "us_per_u_application": round(us, 3),
+                                  "horner_bytes_per_u": 3 * d * b,
+                                  "gbs_algorithmic": round(3 * d * b / us / 1e3, 1)}),
+                      flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="filter_df",
-                    choices=["fp64", "filter_fp32", "filter_df"])
+    ap.add_argument("--precision", default="filter_df", choices=["fp64", "filter_df"])
+    ap.add_argument("--batch", type=int, default=2,
+                    help="eigenproblems per lockstep solve")
+    ap.add_argument("--tol", type=float, default=1e-6,
+                    help="Krylov convergence tolerance of the Ritz values of g_k (the U-residual "
+                         "<= 1e-10 of every returned pair is checked separately)")
     ap.add_argument("--max-restarts", type=int, default=30)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--u-timing", default=None,
+                    help="comma-separated L values: print per-U-application filter times per "
+                         "sweep precision instead of the benchmark line")
     args = ap.parse_args()
+    if args.u_timing:
+        u_timing([int(x) for x in args.u_timing.split(",")])
+        return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -126,6 +126,26 @@ int floquet_apply_u(floquet_t op, const void* psi_in, void* psi_out, int nvec, i
 int filter_apply(floquet_t op, double phi, int64_t k, const void* psi_in, void* psi_out,
                  int nvec, int dtype, int form, void* stream);
 
+/* The correction step of the FP64 polish of the FP32-filter form (Sec. 4 footnote, iterated),
+ * exposed for testing and for callers that refine eigenpairs themselves. For each j < n:
+ *     out_j = q_j(U) r_j,   q_j(U) = sum_{l=0}^{K-2} a_l U^l,
+ *     a_l = z^{l+1} g_{K-1-l}(z omega_j),  z = exp(-i phi),  g_n(w) = sum_{m<n} w^m,
+ * the polynomial with g_K(U) - g_K(omega_j) = q_j(U) (U - omega_j) (Sec. 3, Eq. geo, summed
+ * term by term). For r_j = (U - omega_j) x_j this is g_K(U) x_j - g_K(omega_j) x_j: the
+ * filtered vector formed from the small residual only, so the sweeps' rounding is relative to
+ * ||r_j||. The coefficients are formed in float64 on the host and rounded to the sweep
+ * precision.
+ *   phi   -- filter target; K >= 2 filter length;
+ *   omega -- host, 2n doubles (re, im), any finite values;
+ *   R     -- device, d x n complex128 (r_j at R + j d); out: device, d x n complex128, must not
+ *            overlap R;
+ *   sweep -- FLOQUET_C64 (complex64 sweeps) or FLOQUET_C128_DF (double-float sweeps).
+ * Allocates and frees small scratch; synchronises `stream`. EINVAL for a NULL pointer, n < 1,
+ * K < 2, another sweep type, phi or omega not finite, overlapping R and out, or a brickwork
+ * handle. */
+int floquet_polish_correction(floquet_t op, double phi, int64_t K, const double* omega,
+                              const void* R, void* out, int n, int sweep, void* stream);
+
 /* One classical Gram-Schmidt step with one full reorthogonalisation (CGS2) of Sec. 4's
  * Arnoldi process: w <- (w - V V^H w) / beta, twice projected, for n >= 0 orthonormal
  * columns V (device, d x n complex128, column-major, leading dimension d).

@@ -2,6 +2,7 @@
 // calls into the operator, filter and eigensolver code.
 
 #include <cmath>
+#include <complex>
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -343,6 +344,46 @@ int filter_apply(floquet_t op, double phi, int64_t k, const void* psi_in, void* 
     set_error("filter_apply: bad dtype %d", dtype);
     return FLOQUET_EINVAL;
   }
+  return clear_and(rc);
+  FQ_GUARD_END
+}
+
+int floquet_polish_correction(floquet_t op, double phi, int64_t K, const double* omega,
+                              const void* R, void* out, int n, int sweep, void* stream) {
+  FQ_GUARD_BEGIN
+  if (!op || !omega || !R || !out || n < 1 || K < 2) {
+    set_error("floquet_polish_correction: NULL pointer, n < 1 or K < 2");
+    return FLOQUET_EINVAL;
+  }
+  if (op->brick) {
+    set_error("floquet_polish_correction: kicked-Ising operators only");
+    return FLOQUET_EINVAL;
+  }
+  if (sweep != FLOQUET_C64 && sweep != FLOQUET_C128_DF) {
+    set_error("floquet_polish_correction: sweep must be FLOQUET_C64 or FLOQUET_C128_DF");
+    return FLOQUET_EINVAL;
+  }
+  if (!std::isfinite(phi)) {
+    set_error("floquet_polish_correction: phi not finite");
+    return FLOQUET_EINVAL;
+  }
+  const char* a = (const char*)R;
+  const char* b = (const char*)out;
+  const size_t bytes = (size_t)n * op->d * 16;
+  if (a < b + bytes && b < a + bytes) {
+    set_error("floquet_polish_correction: R and out overlap");
+    return FLOQUET_EINVAL;
+  }
+  std::vector<std::complex<double>> om(n);
+  for (int j = 0; j < n; ++j) {
+    om[j] = std::complex<double>(omega[2 * j], omega[2 * j + 1]);
+    if (!std::isfinite(om[j].real()) || !std::isfinite(om[j].imag())) {
+      set_error("floquet_polish_correction: omega %d not finite", j);
+      return FLOQUET_EINVAL;
+    }
+  }
+  const int rc = polish_correction(op, phi, K, om.data(), (const double2*)R, (double2*)out, n,
+                                   sweep == FLOQUET_C128_DF, (cudaStream_t)stream);
   return clear_and(rc);
   FQ_GUARD_END
 }

@@ -469,240 +469,146 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
 
 // ------------------------------------------------------------------ polish
 
-// Hermitian n x n matrix A (column-major, host) = R^H R by Cholesky with diagonal pivoting:
-// at each step the column with the largest remaining diagonal is taken, until that diagonal
-// falls to `floor` (the remaining columns are dependent on the chosen ones and dropped).
-// piv[0..rank) are the chosen columns in order; R (rank x rank, column-major, upper) acts on
-// them. Returns the rank.
-static int pivoted_cholesky(std::vector<cd> A, int n, double floor, std::vector<int>& piv,
-                            std::vector<cd>& R) {
-  std::vector<int> p(n);
-  std::iota(p.begin(), p.end(), 0);
-  int rank = 0;
-  for (; rank < n; ++rank) {
-    int best = rank;
-    for (int j = rank + 1; j < n; ++j)
-      if (A[(size_t)p[j] * n + p[j]].real() > A[(size_t)p[best] * n + p[best]].real()) best = j;
-    std::swap(p[rank], p[best]);
-    const int c = p[rank];
-    const double dg = A[(size_t)c * n + c].real();
-    if (!(dg > floor)) break;
-    const double r = std::sqrt(dg);
-    // row `rank` of R over the remaining pivot order: R[rank, j] = A[c, p_j] / r
-    for (int j = rank + 1; j < n; ++j) {
-      const int cj = p[j];
-      const cd rij = A[(size_t)cj * n + c] / r;  // A(c, cj)
-      // update the Schur complement A(p_i, p_j) -= conj(R[rank, i]) R[rank, j]
-      for (int i2 = rank + 1; i2 < n; ++i2) {
-        const int ci = p[i2];
-        const cd rii = A[(size_t)ci * n + c] / r;
-        A[(size_t)cj * n + ci] -= std::conj(rii) * rij;
-      }
-    }
-    // keep R's row for the chosen columns, recomputed below from the final order
-    A[(size_t)c * n + c] = cd(r, 0.0);
+// a_l(omega) = z^{l+1} g_{k-1-l}(z omega), l = 0..k-2: the polynomial q with
+// g_k(U) - g_k(omega) = q(U) (U - omega), so that g_k(U) x = g_k(omega) x + q(U) r for
+// r = (U - omega) x. The FP32 sweeps then act on the small residual r only.
+static void defect_coefficients(cd omega, double phi, int64_t k, cd* out, cd* g_at_omega) {
+  const cd z = std::polar(1.0, -phi);
+  const cd w = z * omega;
+  // g_n(w) for n = 1 .. k by g_{n} = g_{n-1} + w^{n-1}
+  std::vector<cd> g(k + 1);
+  g[0] = 0;
+  cd wn = 1;
+  for (int64_t n = 1; n <= k; ++n) {
+    g[n] = g[n - 1] + wn;
+    wn *= w;
   }
-  // R[i, j] over the chosen pivots (i <= j < rank): a second, exact pass from the original
-  // relation A_pp = R^H R is not needed; rebuild R from the updated entries instead
-  piv.assign(p.begin(), p.begin() + rank);
-  return rank;
+  *g_at_omega = g[k];
+  for (int64_t l = 0; l + 1 < k; ++l) {
+    out[l] = std::polar(1.0, -phi * (double)(l + 1)) * g[k - 1 - l];
+  }
 }
 
-// Q = C M with M = R^{-1} on the chosen columns (upper-triangular inverse, host).
-static std::vector<cd> upper_inverse(const std::vector<cd>& R, int r) {
-  std::vector<cd> X((size_t)r * r, cd(0.0, 0.0));
-  for (int j = 0; j < r; ++j) {
-    X[(size_t)j * r + j] = 1.0 / R[(size_t)j * r + j];
-    for (int i = j - 1; i >= 0; --i) {
-      cd sum = 0;
-      for (int l = i + 1; l <= j; ++l) sum += R[(size_t)l * r + i] * X[(size_t)j * r + l];
-      X[(size_t)j * r + i] = -sum / R[(size_t)i * r + i];
+// out_j = q_j(U) r_j for j < n, q_j the defect polynomial of omega_j above with filter length
+// K and target phi: the correction step of the polish, and the C ABI's
+// floquet_polish_correction. Sweeps in complex64 (df = false) or double-float (df = true),
+// the coefficients rounded to that precision; r_j at R + j d, out_j at out + j d (complex128).
+int polish_correction(floquet_op* op, double phi, int64_t K, const cd* omega, const double2* R,
+                      double2* out, int n, bool df, cudaStream_t st) {
+  const int64_t d = op->d;
+  const size_t nc = (size_t)n * (K - 1);
+  std::vector<cd> a((size_t)(K - 1));
+  cd gv;
+  if (df) {
+    std::vector<float4> h(nc);
+    for (int j = 0; j < n; ++j) {
+      defect_coefficients(omega[j], phi, K, a.data(), &gv);
+      for (int64_t l = 0; l + 1 < K; ++l)
+        h[(size_t)j * (K - 1) + l] = from_d2<dfloat>(make_double2(a[l].real(), a[l].imag()));
     }
-  }
-  return X;
-}
-
-// Cholesky R (rank x rank, column-major upper) of the pivoted Hermitian block A[piv, piv].
-static std::vector<cd> cholesky_upper(const std::vector<cd>& A, int n,
-                                      const std::vector<int>& piv) {
-  const int r = (int)piv.size();
-  std::vector<cd> R((size_t)r * r, cd(0.0, 0.0));
-  for (int j = 0; j < r; ++j) {
-    for (int i = 0; i <= j; ++i) {
-      cd sum = A[(size_t)piv[j] * n + piv[i]];  // A(piv_i, piv_j)
-      for (int l = 0; l < i; ++l) sum -= std::conj(R[(size_t)i * r + l]) * R[(size_t)j * r + l];
-      if (i == j) {
-        const double v = sum.real();
-        R[(size_t)j * r + j] = cd(std::sqrt(v > 0 ? v : 0.0), 0.0);
-      } else {
-        R[(size_t)j * r + i] = sum / R[(size_t)i * r + i];
-      }
+    DevBuf<float4> c;
+    FQ_TRY(c.alloc(nc));
+    FQ_CUDA(cudaMemcpyAsync(c.p, h.data(), sizeof(float4) * nc, cudaMemcpyHostToDevice, st));
+    FQ_TRY((filter_coef<dfloat, double>(op, R, d, out, d, c.p, K - 1, n, n, true, st)));
+    FQ_CUDA(cudaStreamSynchronize(st));  // c is freed on return
+  } else {
+    std::vector<float2> h(nc);
+    for (int j = 0; j < n; ++j) {
+      defect_coefficients(omega[j], phi, K, a.data(), &gv);
+      for (int64_t l = 0; l + 1 < K; ++l)
+        h[(size_t)j * (K - 1) + l] = make_float2((float)a[l].real(), (float)a[l].imag());
     }
-  }
-  return R;
-}
-
-// Orthonormalise the nn columns S[:, n0 : n0 + nn] (leading dimension d) against S[:, :n0]
-// (classical Gram-Schmidt, twice) and among themselves (Cholesky QR with diagonal pivoting,
-// twice). Each column is first scaled to unit length; a column whose remaining length after
-// the projections is below `drop` adds no direction and is dropped. The kept columns end up
-// in S[:, n0 : n0 + kept]. T is scratch of d x nn, M of max(n0, nn) x nn complex.
-static int orth_block(Workspace& ws, double2* S, int64_t d, int n0, int nn, double drop,
-                      double2* T, double2* M, int* kept, cudaStream_t st) {
-  *kept = 0;
-  if (nn <= 0) return FLOQUET_OK;
-  double2* C = S + (int64_t)n0 * d;
-  std::vector<double2> g((size_t)nn * nn);
-  auto gram = [&](int n) -> int {  // g = C[:, :n]^H C[:, :n] on the host
-    FQ_TRY(gemm_cn(ws, C, d, 0, C, d, 0, d, n, n, 1, M, n, 0, st));
-    FQ_CUDA(cudaMemcpyAsync(g.data(), M, sizeof(double2) * n * n, cudaMemcpyDeviceToHost, st));
+    DevBuf<float2> c;
+    FQ_TRY(c.alloc(nc));
+    FQ_CUDA(cudaMemcpyAsync(c.p, h.data(), sizeof(float2) * nc, cudaMemcpyHostToDevice, st));
+    FQ_TRY((filter_coef<float, double>(op, R, d, out, d, c.p, K - 1, n, n, true, st)));
     FQ_CUDA(cudaStreamSynchronize(st));
-    return FLOQUET_OK;
-  };
-  // unit columns
-  FQ_TRY(gram(nn));
-  {
-    std::vector<double2> sc(nn);
-    for (int j = 0; j < nn; ++j) {
-      const double v = g[(size_t)j * nn + j].x;
-      sc[j] = make_double2(v > 0 ? 1.0 / std::sqrt(v) : 0.0, 0.0);
-    }
-    FQ_CUDA(cudaMemcpyAsync(M, sc.data(), sizeof(double2) * nn, cudaMemcpyHostToDevice, st));
-    FQ_TRY(scale_cols(C, d, nn, M, st));
   }
-  for (int pass = 0; pass < 2 && n0 > 0; ++pass) {
-    FQ_TRY(gemm_cn(ws, S, d, 0, C, d, 0, d, n0, nn, 1, M, n0, 0, st));  // S^H C
-    FQ_TRY(gemm_nn(S, d, 0, M, n0, 0, T, d, 0, d, n0, nn, 1, st));     // S (S^H C)
-    FQ_TRY(sub_cols(C, d, T, d, d, nn, st));
-  }
-  int n = nn;
-  for (int pass = 0; pass < 2; ++pass) {
-    FQ_TRY(gram(n));
-    std::vector<cd> A((size_t)n * n);
-    for (size_t i = 0; i < A.size(); ++i) A[i] = cd(g[i].x, g[i].y);
-    std::vector<int> piv;
-    std::vector<cd> Rdummy;
-    const int r = pivoted_cholesky(A, n, pass == 0 ? drop * drop : 0.0, piv, Rdummy);
-    if (r == 0) {
-      *kept = 0;
-      return FLOQUET_OK;
-    }
-    const std::vector<cd> R = cholesky_upper(A, n, piv);
-    const std::vector<cd> Ri = upper_inverse(R, r);
-    // Q = C P R^{-1}: M (n x r) holds Ri's rows at the pivot positions
-    std::vector<double2> mh((size_t)n * r, make_double2(0, 0));
-    for (int j = 0; j < r; ++j)
-      for (int i = 0; i <= j; ++i) {
-        const cd v = Ri[(size_t)j * r + i];
-        mh[(size_t)j * n + piv[i]] = make_double2(v.real(), v.imag());
-      }
-    FQ_CUDA(cudaMemcpyAsync(M, mh.data(), sizeof(double2) * n * r, cudaMemcpyHostToDevice, st));
-    FQ_TRY(gemm_nn(C, d, 0, M, n, 0, T, d, 0, d, n, r, 1, st));
-    FQ_CUDA(cudaMemcpyAsync(C, T, sizeof(double2) * d * r, cudaMemcpyDeviceToDevice, st));
-    n = r;
-  }
-  *kept = n;
   return FLOQUET_OK;
 }
 
-// FP64 polish of the FILTER_FP32 result (one problem): the Ritz step with U on approximate
-// eigenvectors that the Sec. 4 footnote suggests, iterated until the U-residuals reach
-// tol_resid.
-//
-// Each iteration: Rayleigh-Ritz with U in complex128 on span(S) (G = S^H U S, its eigen-
-// decomposition on the device); the block = the nb Ritz pairs with the largest |g_k(omega)|
-// (values off the unit circle are mixtures and rank last); stop when the nev in-lobe pairs
-// closest to exp(i phi) have residual <= tol_resid. Otherwise compute a correction for every
-// selected pair still above tol_resid / 10: with r = (U - omega) x formed in FP64 and the
-// filter g_K centred on omega itself,
-//     g_K(U / omega) x - K x = q(U) r,   q(U) = sum_{l < K-1} (K-1-l) omega^{-(l+1)} U^l,
-// (Sec. 3, Eq. geo, the defect of the geometric sum at its own peak), so q(U) r is
-// g_K(U / omega) x with the part along x removed: the error components of x far from omega
-// come back multiplied by about -K, those near omega are suppressed. Only the small residual
-// r goes through the complex64 sweeps (Horner form with the coefficients K-1-l), so their
-// rounding is relative to ||r||. The corrections of all pairs share one batched filter
-// launch; K = k/2 by default (FLOQUET_POLISH_K sets it).
-// The next space is [Ritz block, the last kWindow correction blocks] (an LOBPCG-like window):
-// the earlier blocks carry what the previous corrections found, so the error components that
-// the pairs share keep converging while the space stays bounded. The Ritz block and the kept
-// blocks lie in span(S): they are re-based by a coefficient matrix (no new U applications);
-// only the new corrections need U in FP64.
+// Orthonormalise the columns of X in place, one at a time: each column is normalised, then
+// projected twice against the columns kept so far (CGS2); a column whose new component is
+// below `drop` of its length adds no direction and is dropped (later columns move up).
+// Without the drop, nearly dependent columns would leave the basis non-orthogonal at the
+// drop level / eps ratio and the Rayleigh-Ritz step would mix eigenvectors.
+static int orthonormalize(Workspace& ws, double2* X, int n, int64_t d, double drop, int* kept,
+                          cudaStream_t st) {
+  int w = 0;
+  double beta = 0;
+  for (int j = 0; j < n; ++j) {
+    double2* col = X + (int64_t)w * d;
+    if (j != w)
+      FQ_CUDA(cudaMemcpyAsync(col, X + (int64_t)j * d, sizeof(double2) * d,
+                              cudaMemcpyDeviceToDevice, st));
+    // normalise (no projection), then project against the kept columns
+    FQ_TRY(cgs2(ws, X, d, 0, 0, col, 0, d, 1, nullptr, 0, col, 0, st));
+    FQ_CUDA(cudaMemcpyAsync(&beta, ws.last_betas, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FQ_CUDA(cudaStreamSynchronize(st));
+    if (!(beta > 0)) continue;
+    if (w > 0) {
+      FQ_TRY(cgs2(ws, X, d, 0, w, col, 0, d, 1, nullptr, 0, col, 0, st));
+      FQ_CUDA(cudaMemcpyAsync(&beta, ws.last_betas, sizeof(double), cudaMemcpyDeviceToHost, st));
+      FQ_CUDA(cudaStreamSynchronize(st));
+      if (!(beta > drop)) continue;
+    }
+    ++w;
+  }
+  *kept = w;
+  return FLOQUET_OK;
+}
+
+// FP64 polish of the FILTER_FP32 result (Sec. 4 footnote: a Ritz step with U on approximate
+// eigenvectors, here iterated). Each iteration: Rayleigh-Ritz with U on span(S); keep the nb
+// Ritz pairs with the largest |g_k(omega)| (the block the filter enhances); stop when the nev
+// closest in-lobe pairs have residuals <= tol_resid; otherwise extend S by the
+// defect-corrected filter directions q(U) r of the unconverged pairs, where
+// g_k(U) x = g_k(omega) x + q(U) r and r = (U - omega) x is computed in FP64, so the
+// complex64 sweeps only act on the small residual.
 int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double tol_resid,
-           int max_iter, double2* X0, int nb_in, int64_t d, std::vector<cd>& omega_out,
+           int max_iter, double2* X0, int nb, int64_t d, std::vector<cd>& omega_out,
            std::vector<double>& resid_out, std::vector<int>& cols_out, int* iters,
            cudaStream_t st) {
+  const int n2 = 2 * nb;
   const bool verbose = getenv("FLOQUET_VERBOSE") != nullptr;
-  int64_t K = std::max<int64_t>(2, k / 2);
-  if (const char* e = getenv("FLOQUET_POLISH_K")) K = std::max<int64_t>(2, atoll(e));
-  // block: the wanted pairs and guard directions (the largest |g_k| beyond them)
-  const int nb = std::min(nb_in, nev + std::max(16, nev / 4));
-  // correction blocks kept in the space (3, or fewer so that the space fits the small
-  // eigensolver's 512)
-  int kWindow = 3;
-  if (const char* e = getenv("FLOQUET_POLISH_WINDOW")) kWindow = std::max(1, atoi(e));
-  kWindow = std::min(kWindow, (512 - nb) / std::max(1, nb));
-  if (kWindow < 1) {
-    set_error("polish: nev %d too large for the Rayleigh-Ritz space", nev);
-    return FLOQUET_EINVAL;
-  }
-  const int smax = nb + kWindow * nb;
-  const double drop = 1e-6;
-  DevBuf<double2> S, W, S2, W2, T, M, G, Gt, Yg, Ysel, Mq, lam, eigw, X, UX, R, Cb;
+  DevBuf<double2> S, WS, Xn, G, Yg, lam, eigw, R, corr;
+  // the correction filter q(U) r sums k terms of size up to k |r|: complex64 sweeps round it
+  // at ~u32 k relative to the useful part, double-float sweeps at ~2^-48 k. The polish starts
+  // with complex64 (cheaper) and switches to double-float once the worst selected residual
+  // has not halved over three iterations (both values finite: a shortfall of candidates is
+  // not a stall); FLOQUET_POLISH_SWEEP=c64 or =df fixes the choice, and
+  // FLOQUET_POLISH_DF_FROM=i switches at iteration i.
+  const char* psw = getenv("FLOQUET_POLISH_SWEEP");
+  const bool forced = psw && (strcmp(psw, "c64") == 0 || strcmp(psw, "df") == 0);
+  bool df_corr = forced && strcmp(psw, "df") == 0;
+  int df_from = -1;
+  if (const char* e = getenv("FLOQUET_POLISH_DF_FROM")) df_from = std::max(0, atoi(e));
+  std::vector<double> worst_hist;
   DevBuf<double> rq;
   DevBuf<int> info;
-  DevBuf<float2> zs, hc;
-  DevBuf<float4> zsd, hcd;  // double-float copies for the later correction steps
-  FQ_TRY(S.alloc((size_t)smax * d));
-  FQ_TRY(W.alloc((size_t)smax * d));
-  FQ_TRY(S2.alloc((size_t)smax * d));
-  FQ_TRY(W2.alloc((size_t)smax * d));
-  FQ_TRY(T.alloc((size_t)nb * d));
-  FQ_TRY(M.alloc((size_t)smax * nb));
-  FQ_TRY(G.alloc((size_t)smax * smax));
-  FQ_TRY(Gt.alloc((size_t)smax * smax));
-  FQ_TRY(Yg.alloc((size_t)smax * smax));
-  FQ_TRY(Ysel.alloc((size_t)smax * nb));
-  FQ_TRY(Mq.alloc((size_t)smax * smax));
-  FQ_TRY(lam.alloc(smax));
-  FQ_TRY(eigw.alloc(small_eig_work_elems(smax)));
+  FQ_TRY(S.alloc((size_t)n2 * d));
+  FQ_TRY(WS.alloc((size_t)n2 * d));
+  FQ_TRY(Xn.alloc((size_t)n2 * d));
+  FQ_TRY(G.alloc((size_t)n2 * n2));
+  FQ_TRY(Yg.alloc((size_t)n2 * n2));
+  FQ_TRY(lam.alloc(n2));
+  FQ_TRY(eigw.alloc(small_eig_work_elems(n2)));
   FQ_TRY(info.alloc(1));
-  FQ_TRY(X.alloc((size_t)nb * d));
-  FQ_TRY(UX.alloc((size_t)nb * d));
   FQ_TRY(R.alloc((size_t)nb * d));
-  FQ_TRY(Cb.alloc((size_t)nb * d));
-  FQ_TRY(rq.alloc((size_t)3 * nb));
-  // the correction sweeps run in complex64; FLOQUET_POLISH_DF_FROM = i runs the steps from
-  // the i-th on in double-float instead
-  int df_from = 1 << 30;
-  if (const char* e = getenv("FLOQUET_POLISH_DF_FROM")) df_from = std::max(0, atoi(e));
-  FQ_TRY(zs.alloc(nb));
-  FQ_TRY(hc.alloc((size_t)K));
-  FQ_TRY(zsd.alloc(nb));
-  FQ_TRY(hcd.alloc((size_t)K));
-  {  // Horner coefficients of q: hc[j] = j + 1 (hc[0] unused)
-    std::vector<float2> h((size_t)K);
-    std::vector<float4> hd((size_t)K);
-    for (int64_t j = 0; j < K; ++j) {
-      h[j] = make_float2((float)(j + 1), 0.0f);
-      hd[j] = from_d2<dfloat>(make_double2((double)(j + 1), 0.0));
-    }
-    FQ_CUDA(cudaMemcpyAsync(hc.p, h.data(), sizeof(float2) * K, cudaMemcpyHostToDevice, st));
-    FQ_CUDA(cudaMemcpyAsync(hcd.p, hd.data(), sizeof(float4) * K, cudaMemcpyHostToDevice, st));
-    FQ_CUDA(cudaStreamSynchronize(st));
-  }
-  // initial space: the block of the converged Ritz vectors with the largest |theta|
+  FQ_TRY(corr.alloc((size_t)nb * d));
+  FQ_TRY(rq.alloc((size_t)3 * n2));
+  const double drop = 1e-6;
   FQ_CUDA(cudaMemcpyAsync(S.p, X0, sizeof(double2) * nb * d, cudaMemcpyDeviceToDevice, st));
   int ns = 0;
-  FQ_TRY(orth_block(ws, S.p, d, 0, nb, drop, T.p, M.p, &ns, st));
-  FQ_TRY(apply_u<double>(op, S.p, W.p, ns, ns, st));
-  FQ_TRY(gemm_cn(ws, S.p, d, 0, W.p, d, 0, d, ns, ns, 1, G.p, smax, 0, st));
-  // column ranges of S holding the kept correction blocks, oldest first
-  std::vector<std::pair<int, int>> blocks;
-  std::vector<double2> lam_h(smax);
-  std::vector<double> rq_h(3 * nb);
-  int corrections = 0;
+  FQ_TRY(orthonormalize(ws, S.p, nb, d, drop, &ns, st));
+  std::vector<double> rq_h(3 * n2);
+  std::vector<double2> lam_h(n2);
+  int nk = 0;
   for (int it = 0;; ++it) {
-    FQ_TRY(small_eig_batched(G.p, smax, 0, ns, 1, lam.p, 0, Yg.p, ns, 0, eigw.p, info.p, st));
+    // Rayleigh-Ritz with U on span(S): G = S^H U S = Yg diag(lam) Yg^{-1}
+    FQ_TRY(apply_u<double>(op, S.p, WS.p, ns, ns, st));
+    FQ_TRY(gemm_cn(ws, S.p, d, 0, WS.p, d, 0, d, ns, ns, 1, G.p, ns, 0, st));
+    FQ_TRY(small_eig_batched(G.p, ns, 0, ns, 1, lam.p, 0, Yg.p, ns, 0, eigw.p, info.p, st));
     int info_h = 0;
     FQ_CUDA(cudaMemcpyAsync(lam_h.data(), lam.p, sizeof(double2) * ns, cudaMemcpyDeviceToHost,
                             st));
@@ -712,35 +618,38 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
       set_error("polish: small eigensolver did not converge (n = %d)", ns);
       return FLOQUET_ENOCONV;
     }
-    // the block: nk Ritz values with the largest |g_k|, values on the unit circle first
-    const int nk = std::min(nb, ns);
+    // keep the nk = min(nb, ns) Ritz values with the largest |g_k(omega)|
+    nk = std::min(nb, ns);
     std::vector<int> order(ns);
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> gabs(ns);
+    // Ritz values off the unit circle are mixtures (a converged pair with ||omega| - 1|
+    // ~ resid^2 / 2 is far closer to it); rank them after every value on the circle
     for (int i = 0; i < ns; ++i) {
       const cd l(lam_h[i].x, lam_h[i].y);
       gabs[i] = std::abs(gk_value(l, phi, k));
       if (std::fabs(std::abs(l) - 1.0) > 1e-8) gabs[i] *= 1e-6;
     }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gabs[a] > gabs[b]; });
+    order.resize(nk);
     for (int i = 0; i < nk; ++i)
-      FQ_CUDA(cudaMemcpyAsync(Ysel.p + (size_t)i * ns, Yg.p + (size_t)order[i] * ns,
+      FQ_CUDA(cudaMemcpyAsync(G.p + (size_t)i * ns, Yg.p + (size_t)order[i] * ns,
                               sizeof(double2) * ns, cudaMemcpyDeviceToDevice, st));
-    FQ_TRY(gemm_nn(S.p, d, 0, Ysel.p, ns, 0, X.p, d, 0, d, ns, nk, 1, st));
-    // U X by a fresh FP64 application (not W Y): the residuals do not depend on how
-    // accurately the re-based W still equals U S
-    FQ_TRY(apply_u<double>(op, X.p, UX.p, nk, nk, st));
-    FQ_TRY(rayleigh_residual(ws, X.p, UX.p, d, nk, rq.p, st));
+    FQ_TRY(gemm_nn(S.p, d, 0, G.p, ns, 0, Xn.p, d, 0, d, ns, nk, 1, st));
+    FQ_TRY(gemm_nn(WS.p, d, 0, G.p, ns, 0, corr.p, d, 0, d, ns, nk, 1, st));  // U Xn
+    FQ_TRY(rayleigh_residual(ws, Xn.p, corr.p, d, nk, rq.p, st));
     FQ_CUDA(cudaMemcpyAsync(rq_h.data(), rq.p, sizeof(double) * 3 * nk, cudaMemcpyDeviceToHost,
                             st));
     FQ_CUDA(cudaStreamSynchronize(st));
-    std::vector<cd> om(nk), om_c(nk);
-    for (int i = 0; i < nk; ++i) {
-      om[i] = cd(rq_h[3 * i], rq_h[3 * i + 1]);
-      // an eigenpair with residual r has ||omega| - 1| ~ r^2 / 2: values farther off the
-      // circle are mixtures, not candidates
+    std::vector<cd> om(nk);
+    for (int i = 0; i < nk; ++i) om[i] = cd(rq_h[3 * i], rq_h[3 * i + 1]);
+    // Rayleigh-Ritz over an extended space also yields mixtures of eigenvectors whose
+    // Rayleigh quotients sit inside the unit disk; an eigenpair with residual r has
+    // ||omega| - 1| ~ r^2 / 2, so only values within 1e-8 of the circle (residual below
+    // ~1e-4) inside the main lobe are candidates.
+    std::vector<cd> om_c(nk);
+    for (int i = 0; i < nk; ++i)
       om_c[i] = std::fabs(std::abs(om[i]) - 1.0) < 1e-8 ? om[i] : cd(0.0, 0.0);
-    }
     const std::vector<int> sel = select_closest(om_c, phi, k, nev, true);
     double worst = sel.size() < (size_t)nev ? INFINITY : 0.0;
     for (int i : sel) worst = std::max(worst, rq_h[3 * i + 2]);
@@ -752,125 +661,54 @@ int polish(floquet_op* op, Workspace& ws, double phi, int64_t k, int nev, double
       resid_out.push_back(rq_h[3 * i + 2]);
     }
     *iters = it;
-    // pairs to correct: every block member still above a tenth of the target, the guard
-    // directions included (a guard left unconverged would mix back into the nearly degenerate
-    // wanted pairs at the next Rayleigh-Ritz step)
+    // residual vectors of the pairs still above a tenth of the target (the others are
+    // locked: they stay in the Rayleigh-Ritz space but are not filtered again)
     std::vector<int> act;
     for (int i = 0; i < nk; ++i)
       if (rq_h[3 * i + 2] > 0.1 * tol_resid) act.push_back(i);
     const int nf = (int)act.size();
-    if (verbose)
-      fprintf(stderr, "floquet polish: iter %d space %d block %d worst selected resid %.3e "
-              "(candidates %zu), correcting %d (K = %lld)\n", it, ns, nk, worst, sel.size(), nf,
-              (long long)K);
+    if (verbose) {
+      fprintf(stderr, "floquet polish: iter %d space %d block %d worst selected resid %.3e, "
+              "filtering %d\n", it, ns, nk, worst, nf);
+      int wi = -1;
+      for (int i : sel)
+        if (wi < 0 || rq_h[3 * i + 2] > rq_h[3 * wi + 2]) wi = i;
+      if (wi >= 0)
+        fprintf(stderr, "  worst pair: block index %d |omega|-1 %.2e angle %.4e |g| %.4e "
+                "(block |g| range %.4e .. %.4e), candidates %d\n", wi,
+                std::abs(om[wi]) - 1.0, wrapped_angle(om[wi], phi),
+                std::abs(gk_value(om[wi], phi, k)), gabs[order[0]], gabs[order[nk - 1]],
+                (int)sel.size());
+    }
+    worst_hist.push_back(worst);
+    const bool stalled = it >= 3 && std::isfinite(worst) && std::isfinite(worst_hist[it - 3]) &&
+                         !(worst < 0.5 * worst_hist[it - 3]);
+    if (!forced && !df_corr && (stalled || (df_from >= 0 && it >= df_from))) {
+      df_corr = true;  // complex64 corrections have stalled (or the switch is requested)
+      if (verbose)
+        fprintf(stderr, "floquet polish: switching to double-float corrections at iteration %d\n",
+                it);
+    }
     if (worst <= tol_resid || it >= max_iter || nf == 0) {
-      FQ_CUDA(cudaMemcpyAsync(X0, X.p, sizeof(double2) * nk * d, cudaMemcpyDeviceToDevice, st));
+      FQ_CUDA(cudaMemcpyAsync(X0, Xn.p, sizeof(double2) * nk * d, cudaMemcpyDeviceToDevice, st));
       break;
     }
-    // residual vectors of the pairs to correct, then q(U) r in one batched filter launch
-    FQ_TRY(residual_vectors(X.p, UX.p, R.p, d, nk, rq.p, st));
-    for (int j = 0; j < nf; ++j)
-      FQ_CUDA(cudaMemcpyAsync(T.p + (size_t)j * d, R.p + (size_t)act[j] * d,
-                              sizeof(double2) * d, cudaMemcpyDeviceToDevice, st));
-    std::vector<float2> zh(nf);
-    std::vector<float4> zhd(nf);
+    FQ_TRY(residual_vectors(Xn.p, corr.p, R.p, d, nk, rq.p, st));
+    std::vector<cd> om_act(nf);
     for (int j = 0; j < nf; ++j) {
-      const cd z = 1.0 / om[act[j]];
-      zh[j] = make_float2((float)z.real(), (float)z.imag());
-      zhd[j] = from_d2<dfloat>(make_double2(z.real(), z.imag()));
+      const int i = act[j];
+      if (i != j)
+        FQ_CUDA(cudaMemcpyAsync(R.p + (size_t)j * d, R.p + (size_t)i * d, sizeof(double2) * d,
+                                cudaMemcpyDeviceToDevice, st));
+      om_act[j] = om[i];
     }
-    if (it >= df_from) {
-      FQ_CUDA(cudaMemcpyAsync(zsd.p, zhd.data(), sizeof(float4) * nf, cudaMemcpyHostToDevice,
-                              st));
-      FQ_CUDA(cudaStreamSynchronize(st));
-      FQ_TRY((filter_horner_coef<dfloat, double>(op, T.p, d, Cb.p, d, zsd.p, hcd.p, K - 1, nf,
-                                                 st)));
-    } else {
-      FQ_CUDA(cudaMemcpyAsync(zs.p, zh.data(), sizeof(float2) * nf, cudaMemcpyHostToDevice,
-                              st));
-      FQ_CUDA(cudaStreamSynchronize(st));
-      FQ_TRY((filter_horner_coef<float, double>(op, T.p, d, Cb.p, d, zs.p, hc.p, K - 1, nf,
-                                                st)));
-    }
-    corrections += nf;
-    // re-base the kept part of the space, [Ritz block, the newest kWindow - 1 correction
-    // blocks] = S Z, by an orthonormal coefficient matrix Mq spanning the columns of Z in that
-    // order (Gram-Schmidt twice on the host; a column whose remaining length is below 1e-8 is
-    // dropped), so that each kept block's remainder stays a contiguous range of columns
-    {
-      while ((int)blocks.size() > kWindow - 1) blocks.erase(blocks.begin());
-      int nz = nk;
-      for (auto& b : blocks) nz += b.second;
-      std::vector<double2> yh((size_t)ns * nk);
-      FQ_CUDA(cudaMemcpyAsync(yh.data(), Ysel.p, sizeof(double2) * ns * nk,
-                              cudaMemcpyDeviceToHost, st));
-      FQ_CUDA(cudaStreamSynchronize(st));
-      std::vector<cd> q((size_t)ns * nz);
-      int nq = 0;
-      std::vector<cd> col(ns);
-      std::vector<std::pair<int, int>> nblocks;
-      int c = 0;
-      for (int g = -1; g < (int)blocks.size(); ++g) {
-        const int gcols = g < 0 ? nk : blocks[g].second;
-        const int start = nq;
-        for (int cc = 0; cc < gcols; ++cc, ++c) {
-          for (int r = 0; r < ns; ++r)
-            col[r] = g < 0 ? cd(yh[(size_t)cc * ns + r].x, yh[(size_t)cc * ns + r].y)
-                           : (r == blocks[g].first + cc ? cd(1.0, 0.0) : cd(0.0, 0.0));
-          double n0 = 0;
-          for (int r = 0; r < ns; ++r) n0 += std::norm(col[r]);
-          n0 = std::sqrt(n0);
-          if (!(n0 > 0)) continue;
-          for (int pass = 0; pass < 2; ++pass)
-            for (int j2 = 0; j2 < nq; ++j2) {
-              const cd* qj = &q[(size_t)j2 * ns];
-              cd h = 0;
-              for (int r = 0; r < ns; ++r) h += std::conj(qj[r]) * col[r];
-              for (int r = 0; r < ns; ++r) col[r] -= h * qj[r];
-            }
-          double n1 = 0;
-          for (int r = 0; r < ns; ++r) n1 += std::norm(col[r]);
-          n1 = std::sqrt(n1);
-          if (!(n1 > 1e-8 * n0)) continue;
-          for (int r = 0; r < ns; ++r) q[(size_t)nq * ns + r] = col[r] / n1;
-          ++nq;
-        }
-        if (g >= 0 && nq > start) nblocks.push_back({start, nq - start});
-      }
-      blocks = nblocks;
-      std::vector<double2> mq((size_t)ns * nq);
-      for (size_t t = 0; t < mq.size(); ++t) mq[t] = make_double2(q[t].real(), q[t].imag());
-      FQ_CUDA(cudaMemcpyAsync(Mq.p, mq.data(), sizeof(double2) * ns * nq,
-                              cudaMemcpyHostToDevice, st));
-      FQ_TRY(gemm_nn(S.p, d, 0, Mq.p, ns, 0, S2.p, d, 0, d, ns, nq, 1, st));
-      FQ_TRY(gemm_nn(W.p, d, 0, Mq.p, ns, 0, W2.p, d, 0, d, ns, nq, 1, st));
-      // G <- Mq^H G Mq
-      FQ_TRY(small_gemm_batched('N', 'N', ns, nq, ns, G.p, smax, 0, Mq.p, ns, 0, Gt.p, smax, 0,
-                                1, st));
-      FQ_TRY(small_gemm_batched('C', 'N', nq, nq, ns, Mq.p, ns, 0, Gt.p, smax, 0, G.p, smax, 0,
-                                1, st));
-      std::swap(S.p, S2.p);
-      std::swap(W.p, W2.p);
-      ns = nq;
-    }
-    // append the new corrections, orthonormalised against the re-based space
-    double2* Cdst = S.p + (size_t)ns * d;
-    FQ_CUDA(cudaMemcpyAsync(Cdst, Cb.p, sizeof(double2) * nf * d, cudaMemcpyDeviceToDevice,
-                            st));
-    int nc = 0;
-    FQ_TRY(orth_block(ws, S.p, d, ns, nf, drop, T.p, M.p, &nc, st));
-    if (nc > 0) blocks.push_back({ns, nc});
-    if (nc > 0) {
-      FQ_TRY(apply_u<double>(op, Cdst, W.p + (size_t)ns * d, nc, nc, st));
-      // G[:ns, ns:ns+nc] = S_old^H W_new; G[ns:ns+nc, :ns+nc] = S_new^H W
-      FQ_TRY(gemm_cn(ws, S.p, d, 0, W.p + (size_t)ns * d, d, 0, d, ns, nc, 1,
-                     G.p + (size_t)ns * smax, smax, 0, st));
-      FQ_TRY(gemm_cn(ws, Cdst, d, 0, W.p, d, 0, d, nc, ns + nc, 1, G.p + ns, smax, 0, st));
-      ns += nc;
-    }
+    FQ_TRY(polish_correction(op, phi, k, om_act.data(), R.p, corr.p, nf, df_corr, st));
+    // span(S) = span(Xn, g_k(U) Xn_active) = span(Xn, corr_active)
+    FQ_CUDA(cudaMemcpyAsync(S.p, Xn.p, sizeof(double2) * nk * d, cudaMemcpyDeviceToDevice, st));
+    FQ_CUDA(cudaMemcpyAsync(S.p + (size_t)nk * d, corr.p, sizeof(double2) * nf * d,
+                            cudaMemcpyDeviceToDevice, st));
+    FQ_TRY(orthonormalize(ws, S.p, nk + nf, d, drop, &ns, st));
   }
-  if (verbose) fprintf(stderr, "floquet polish: %d corrections of %lld terms\n", corrections,
-                       (long long)(K - 1));
   return FLOQUET_OK;
 }
 

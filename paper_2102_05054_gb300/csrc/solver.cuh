@@ -49,4 +49,10 @@ int krylov_schur(floquet_op* op, int B, int vpp, const double* phis, int64_t k, 
                  const double2* v0_dev, std::vector<KSOut>& out, cudaStream_t st,
                  KSStats* stats);
 
+// The polish's correction step: out_j = q_j(U) r_j with q_j the defect polynomial of the
+// k-term filter at target phi and Ritz value omega[j] (g_k(U) - g_k(omega_j) = q_j(U)(U - omega_j)),
+// in complex64 (df = false) or double-float (df = true) sweeps; R and out are d x n complex128.
+int polish_correction(floquet_op* op, double phi, int64_t K, const std::complex<double>* omega,
+                      const double2* R, double2* out, int n, bool df, cudaStream_t st);
+
 }  // namespace fq

@@ -28,7 +28,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "floquet_internal.cuh"
@@ -477,9 +479,10 @@ __global__ void phase_table_kernel(const double2* __restrict__ tlo, const double
   }
 }
 
-// The persistent kernel's full phase table for double-float sweeps with up to 2^23 table
-// entries (*out stays null otherwise, and for the other precisions, whose sweeps are bound by
-// data movement rather than arithmetic).
+// The full phase table z D_s per vector for double-float sweeps with up to 2^23 table entries
+// (*out stays null otherwise, and for the other precisions, whose sweeps are bound by data
+// movement rather than arithmetic). Cached filter graphs hold the table's address: a
+// reallocation drops them.
 template <typename Real>
 static int build_phase_table(floquet_op* op, const cplx<Real>* zs, int nvec, int vpp,
                              cudaStream_t st, const cplx<Real>** out) {
@@ -489,6 +492,7 @@ static int build_phase_table(floquet_op* op, const cplx<Real>* zs, int nvec, int
     return FLOQUET_OK;
   const size_t pbytes = (size_t)nvec * d * sizeof(cplx<Real>);
   if (op->ptab_bytes < pbytes) {
+    destroy_graphs(op);
     cudaFree(op->ptab);
     op->ptab = nullptr;
     op->ptab_bytes = 0;
@@ -554,6 +558,19 @@ static HornerGridArgs<Real> grid_args(floquet_op* op, const cplx<Real>* pin, cpl
 // operator's cached graphs when it changes the plan. FLOQUET_PASS_VARIANT=<i> pins a shape
 // and FLOQUET_FILTER_KERNEL=grid|pass the filter kernel, with FLOQUET_GRID_SHAPE=<i> the
 // persistent kernel's shape (profiling, tests).
+// Process-wide memory of the tuner's choices per (device, L, sweep precision, timed batch
+// width): operators of the same geometry take the stored choice instead of timing again (the
+// choice depends on the launch geometry, not on the field values), which also keeps the
+// choice stable from one operator to the next.
+struct TuneKey {
+  int dev, L, dtype, nt;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, L, dtype, nt) < std::tie(o.dev, o.L, o.dtype, o.nt);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune_memo;  // -> (pass variant, grid shape)
+
 template <typename Real> static int tune(floquet_op* op, int nvec, cudaStream_t st) {
   const int t = sweep_dtype<Real>();
   if (op->tuned[t]) return FLOQUET_OK;
@@ -582,6 +599,20 @@ template <typename Real> static int tune(floquet_op* op, int nvec, cudaStream_t 
   // time with the caller's batch width (capped), since the best tile depends on how many
   // CTAs the whole launch has
   const int nt = std::max(1, std::min(nvec, std::max(1, (int)((int64_t(64) << 20) / op->d))));
+  int dev = 0;
+  FQ_CUDA(cudaGetDevice(&dev));
+  const TuneKey key{dev, op->L, t, nt};
+  const bool memo_ok = !forced && !grid_forced;
+  if (memo_ok) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tune_memo.find(key);
+    if (it != g_tune_memo.end()) {
+      set_variant<Real>(op, it->second.first);
+      op->gshape[t] = it->second.second;
+      destroy_graphs(op);
+      return FLOQUET_OK;
+    }
+  }
   cplx<Real>* buf = nullptr;
   FQ_CUDA(cudaMalloc(&buf, 2 * sizeof(cplx<Real>) * op->d * nt));
   cplx<Real>* pin = buf;
@@ -652,6 +683,10 @@ template <typename Real> static int tune(floquet_op* op, int nvec, cudaStream_t 
   cudaStreamSynchronize(st);
   cudaFree(buf);
   destroy_graphs(op);
+  if (rc == FLOQUET_OK && memo_ok) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_memo[key] = std::make_pair(op->variant[t], op->gshape[t]);
+  }
   return rc;
 }
 
@@ -932,6 +967,9 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
   }
   FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, pin, acc, nullptr, 0, d, nvec, st)));
   const int np = (int)plan_of<Real>(op).passes.size();
+  // (the per-pass kernels form z D_s from the two chunk tables: a full per-amplitude table
+  // read from L2 measured slower here, 30.9 against 29.4 us per vector-U at L = 20 with two
+  // double-float vectors, than the arithmetic it saves)
   auto body = [&](cudaStream_t s) -> int {
     for (int64_t j = 1; j < k; ++j)
       FQ_TRY(u_passes<Real>(op, acc, acc, nvec, vec_per_prob, EPI_PHASE_HORNER, nullptr,

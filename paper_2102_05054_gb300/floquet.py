@@ -36,6 +36,8 @@ SIGNATURES = {
     "filter_apply": (_c_int, [_c_void_p, _c_double, _c_int64, _c_void_p, _c_void_p, _c_int,
                               _c_int, _c_int, _c_void_p]),
     "gram_schmidt": (_c_int, [_c_int64, _c_void_p, _c_int, _c_void_p, _dptr, _c_void_p]),
+    "floquet_polish_correction": (_c_int, [_c_void_p, _c_double, _c_int64, _dptr, _c_void_p,
+                                           _c_void_p, _c_int, _c_int, _c_void_p]),
     "gram_schmidt_noalloc": (_c_int, [_c_int64, _c_void_p, _c_int, _c_void_p, _c_void_p,
                                       _c_void_p]),
     "small_eig": (_c_int, [_c_int, _c_void_p, _dptr, _c_void_p, _c_void_p]),
@@ -201,6 +203,20 @@ class Floquet:
                                   self._nvec(psi_in), dt, int(form), _stream(stream)),
                "filter_apply")
         return psi_out
+
+    def polish_correction(self, phi, K, omega, R, out, sweep=C64, stream=None):
+        """out_j = q_j(U) R_j, q_j the defect polynomial of the K-term filter at phi and
+        omega_j; R, out: device complex128 tensors of nvec states; omega: nvec complex
+        numbers; sweep: C64 or C128_DF."""
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.complex128).ravel())
+        n = self._nvec(R)
+        if om.size != n:
+            raise ValueError("one omega per state")
+        _check(lib().floquet_polish_correction(self.handle, float(phi), int(K),
+                                               om.view(np.float64).ctypes.data_as(_dptr),
+                                               _ptr(R), _ptr(out), n, int(sweep),
+                                               _stream(stream)), "floquet_polish_correction")
+        return out
 
     def ritz_residuals(self, X, stream=None):
         n = self._nvec(X)

@@ -72,6 +72,8 @@ def test_calls_reject_null_handles(lib):
     assert lib.small_eig(0, None, None, None, None) == floquet.EINVAL
     assert lib.small_eig(513, None, None, None, None) == floquet.EINVAL
     assert lib.gram_schmidt(0, None, 0, None, None, None) == floquet.EINVAL
+    assert lib.floquet_polish_correction(None, 0.0, 8, None, None, None, 1, 1,
+                                         None) == floquet.EINVAL
 
 
 def test_launch_counter_resets(lib):

@@ -1,7 +1,9 @@
 """Parity at the full size of the L = 20 workload, in the launch configuration bench.py times
 (L = 20, k = 16384, m = 256, nev = 100, phi = 0, double-float sweeps): the oracle cannot
 diagonalise d = 2^20, so the returned pairs are checked one by one with the oracle's own
-float64 U (sampled residuals), plus properties that hold at any size.
+float64 U (Rayleigh quotient and residual of all nev pairs, one vector at a time), plus
+properties that hold at any size, and completeness: a second solve with half the filter
+length returns the same nev eigenvalues.
 """
 
 import math
@@ -9,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import geosum, krylov, model
+from oracle import krylov, model
 from paper_2102_05054_gb300 import inputs
 
 from gpu_util import from_dev, require_gpu, to_dev
@@ -34,16 +36,19 @@ def test_L20_workload_full_size_sampled_residuals():
     assert np.abs(np.abs(om) - 1).max() < 1e-10
     ang = np.abs(np.angle(om * np.exp(-1j * phi)))
     assert np.all(np.diff(ang) >= 0) and ang.max() < 2 * math.pi / k
-    # the oracle's U on sampled eigenvectors (first, middle, last = the least separated)
+    # every pair by the oracle's float64 U: Rayleigh quotient and residual
     op = model.KickedIsing(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h)
     X = from_dev(ev, 1 << L)
-    for i in (0, nev // 2, nev - 1):
-        x = X[:, i] / np.linalg.norm(X[:, i])
-        ux = op.apply_u(x)
-        omega = np.vdot(x, ux)
-        assert abs(omega - om[i]) < 1e-12
-        assert np.linalg.norm(ux - omega * x) <= 1e-10
-    # distinct eigenvectors: the sampled ones are mutually orthogonal
-    S = X[:, [0, nev // 2, nev - 1]]
-    G = S.conj().T @ S
-    assert np.abs(G - np.diag(np.diag(G))).max() < 1e-9
+    om_cpu, r_cpu, Xn = krylov.rayleigh_residual(op, X)
+    assert np.abs(om_cpu - om).max() < 1e-12
+    assert r_cpu.max() <= 1e-10
+    # distinct eigenvectors: an orthonormal set
+    G = Xn.conj().T @ Xn
+    assert np.abs(G - np.eye(nev)).max() < 1e-9
+    del X, Xn, G, ev
+    # completeness: a second solve with half the filter length (a lobe twice as wide, so a
+    # different Krylov space) returns the same 100 eigenvalues
+    om2, res2, nconv2, rc2 = fq.arnoldi_eigs(phi, k // 2, nev, m, v0, precision=floquet.FILTER_DF)
+    assert rc2 == floquet.OK and nconv2 == nev and res2.max() <= 1e-10
+    dev = np.abs(np.sort_complex(om)[:, None] - om2[None, :]).min(axis=1).max()
+    assert dev <= 1e-10, dev

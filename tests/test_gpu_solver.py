@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import krylov, model
+from oracle import geosum, krylov, model
 from paper_2102_05054_gb300 import inputs
 
 from gpu_util import from_dev, require_gpu, to_dev
@@ -264,3 +264,144 @@ def test_arnoldi_eigs_invariant_start_vector():
     for w, r in zip(om, res):
         assert (abs(abs(w) - 1) < 1e-12 and r < 1e-12) or (w == 0 and np.isinf(r))
     _ = torch
+
+
+@pytest.mark.parametrize("sweep", ["c64", "df"])
+@pytest.mark.parametrize("K", [2, 3, 64, 257])
+def test_polish_correction_matches_oracle_defect_coefficients(K, sweep):
+    # out_j = q_j(U) r_j with the oracle's defect coefficients a_l(omega_j) at target phi,
+    # for Ritz values on the circle (at and away from the target) and inside / outside it
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    L, phi = 10, 0.4
+    h = inputs.disorder(L, 1.0, 21)
+    fq = floquet.Floquet(L, 1.0, 0.9045, h)
+    op = model.KickedIsing(L, 1.0, 0.9045, h)
+    omega = np.array([np.exp(0.4j), np.exp(-2.0j), 0.999 * np.exp(0.7j), 1.001 * np.exp(0.41j)])
+    n = omega.size
+    X = inputs.random_states(1 << L, n, 5)
+    R = op.apply_u_block(X) - X * omega
+    want = np.zeros_like(R)
+    for j in range(n):
+        a = geosum.defect_coefficients(omega[j], phi, K)
+        p = R[:, j].copy()
+        for l in range(K - 1):
+            want[:, j] += a[l] * p
+            p = op.apply_u(p)
+    tR = to_dev(R)
+    tout = torch.empty_like(tR)
+    fq.polish_correction(phi, K, omega, tR, tout,
+                         sweep=floquet.C64 if sweep == "c64" else floquet.C128_DF)
+    torch.cuda.synchronize()
+    got = from_dev(tout, 1 << L)
+    # ~(L + 3) roundings per U application, accumulated over K - 1 terms
+    u = 6e-8 if sweep == "c64" else 4e-15
+    tol = 4 * u * (L + 3) * math.sqrt(K)
+    for j in range(n):
+        assert np.abs(got[:, j] - want[:, j]).max() <= tol * np.abs(want[:, j]).max(), j
+    assert np.array_equal(from_dev(tR, 1 << L), R)  # the input is left untouched
+
+
+def test_polish_correction_rejections():
+    torch = require_gpu()
+    from paper_2102_05054_gb300 import floquet
+    fq = floquet.Floquet(9, 0.7, 0.4, inputs.disorder(9, 2.0, 3))
+    omega = np.array([1.0, 1j])
+    tR = to_dev(inputs.random_states(1 << 9, 2, 9))
+    tout = torch.empty_like(tR)
+    with pytest.raises(RuntimeError):
+        fq.polish_correction(0.0, 1, omega, tR, tout)                      # K < 2
+    with pytest.raises(RuntimeError):
+        fq.polish_correction(0.0, 8, omega, tR, tout, sweep=floquet.C128)  # sweep type
+    with pytest.raises(RuntimeError):
+        fq.polish_correction(0.0, 8, np.array([np.nan, 1.0]), tR, tout)    # omega not finite
+    with pytest.raises(RuntimeError):
+        fq.polish_correction(0.0, 8, omega, tR, tR)                        # out overlaps R
+
+
+def test_fp32_filter_form_with_double_float_corrections_L12(monkeypatch):
+    # the polish with its correction sweeps fixed to double-float (by default it starts in
+    # complex64 and switches once the worst residual stops halving)
+    monkeypatch.setenv("FLOQUET_POLISH_SWEEP", "df")
+    om, res, nconv, rc, X, op = _solve(12, 1.0, 0.9045, 1.0, 2, 0.0, 128, 24, 96, precision=1)
+    assert rc == 0 and nconv == 24
+    _check_against_dense(om, res, X, op, 0.0, 24)
+
+
+def test_fp32_filter_form_switches_corrections_mid_polish_L12(monkeypatch, capfd):
+    # complex64 corrections first, double-float from the polish's second iteration on: the
+    # switch happens inside the loop (the library reports it on stderr when verbose)
+    monkeypatch.setenv("FLOQUET_POLISH_DF_FROM", "1")
+    monkeypatch.setenv("FLOQUET_VERBOSE", "1")
+    om, res, nconv, rc, X, op = _solve(12, 1.0, 0.9045, 1.0, 2, 0.0, 128, 24, 96, precision=1)
+    err = capfd.readouterr().err
+    assert rc == 0 and nconv == 24
+    _check_against_dense(om, res, X, op, 0.0, 24)
+    if "floquet polish: iter 1 " in err:   # the polish ran past its first iteration
+        assert "switching to double-float corrections at iteration 1" in err
+
+
+@pytest.mark.parametrize("name,other", [("kicked_ising_L16", 0), ("kicked_ising_L18_fp32filter", 2)])
+def test_fp32_filter_form_at_configs_L16_L18(name, other):
+    # the FP32-filter form at the L = 16 and L = 18 configurations: every returned residual
+    # <= 1e-10 by the oracle's U, eigenvalues equal to the FP64 (L = 16) or double-float
+    # (L = 18) form's to 1e-10
+    cfg = inputs.WORKLOADS[name]
+    L, W, seed, phi = cfg["L"], cfg["W"], cfg["seed"], cfg["phi"]
+    k, m, nev = cfg["k"], cfg["m"], cfg["nev"]
+    om, res, nconv, rc, X, op = _solve(L, 1.0, 0.9045, W, seed, phi, k, nev, m, precision=1)
+    assert rc == 0 and nconv == nev and res.max() <= 1e-10
+    om_cpu, r_cpu, _ = krylov.rayleigh_residual(op, X)
+    assert np.abs(om_cpu - om).max() < 1e-12
+    assert r_cpu.max() <= 1e-10
+    om2, res2, nconv2, rc2, _, _ = _solve(L, 1.0, 0.9045, W, seed, phi, k, nev, m,
+                                          precision=other)
+    assert rc2 == 0 and nconv2 == nev
+    ok, dev = _same_set(om, om2, 1e-10)
+    assert ok, dev
+
+
+def _angles(om, phi):
+    return np.abs(np.angle(om * np.exp(-1j * phi)))
+
+
+def _same_set(a, b, tol):
+    """Every eigenvalue of a matches one of b to tol (unit-circle values, so sort by angle)."""
+    a = np.sort_complex(a)
+    d = np.abs(a[:, None] - b[None, :]).min(axis=1)
+    return d.max() <= tol, d.max()
+
+
+def test_config_L16_oracle_residuals_and_completeness():
+    # the physical L = 16 configuration (h ~ U[-2, 2], phi = pi/3, k = 1024, m = 160, nev = 50)
+    cfg = inputs.WORKLOADS["kicked_ising_L16"]
+    L, W, seed, phi = cfg["L"], cfg["W"], cfg["seed"], cfg["phi"]
+    k, m, nev = cfg["k"], cfg["m"], cfg["nev"]
+    om, res, nconv, rc, X, op = _solve(L, 1.0, 0.9045, W, seed, phi, k, nev, m)
+    assert rc == 0 and nconv == nev and res.max() <= 1e-10
+    # every pair, by the oracle's U: Rayleigh quotient and residual
+    om_cpu, r_cpu, _ = krylov.rayleigh_residual(op, X)
+    assert np.abs(om_cpu - om).max() < 1e-12
+    assert r_cpu.max() <= 1e-10
+    assert np.abs(X.conj().T @ X - np.eye(nev)).max() < 1e-9
+    # completeness: a second solve with half the filter length returns the same 50 values
+    om2, res2, nconv2, rc2, _, _ = _solve(L, 1.0, 0.9045, W, seed, phi, k // 2, nev, m)
+    assert rc2 == 0 and nconv2 == nev
+    ok, dev = _same_set(om, om2, 1e-10)
+    assert ok, dev
+    # ... and solves centred at phi -/+ delta agree with it on every value nearer to phi than
+    # their own farthest one (a missed eigenvalue would show up in one set and not the other)
+    delta = 0.25 * _angles(om, phi).max()
+    for s in (-1.0, 1.0):
+        ps = phi + s * delta
+        om3, res3, nconv3, rc3, _, _ = _solve(L, 1.0, 0.9045, W, seed, ps, k, nev, m)
+        assert rc3 == 0 and nconv3 == nev and res3.max() <= 1e-10
+        a3 = _angles(om3, ps)
+        reach = a3.max()
+        inside = np.abs(np.angle(om * np.exp(-1j * ps))) < reach - 1e-9
+        assert inside.sum() >= nev // 2
+        ok, dev = _same_set(om[inside], om3, 1e-10)
+        assert ok, dev
+        back = _angles(om3, phi) < _angles(om, phi).max() - 1e-9
+        ok, dev = _same_set(om3[back], om, 1e-10)
+        assert ok, dev

@@ -247,6 +247,33 @@ def test_arnoldi_relation():
     assert np.abs(V[:, :m].conj().T @ AV - H[:m]).max() < 1e-12 * np.abs(H).max()
 
 
+def test_rayleigh_residual_identity_off_eigenvectors():
+    # For unitary U and a unit vector x that is NOT an eigenvector, omega = <x|U|x> and
+    # ||U x - omega x||^2 = ||U x||^2 - 2 Re(conj(omega) <x|U x>) + |omega|^2 = 1 - |omega|^2
+    # (exact algebra, independent of the code). A residual that dropped the omega term,
+    # returned its square, or forgot the normalisation of x fails it; so does omega taken as
+    # <Ux|x> (its conjugate) unless the residual is also computed with that conjugate.
+    L = 8
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 21))
+    X = inputs.random_states(1 << L, 6, 40) * np.array([1.0, 3.0, 0.25, 1.0, 7.0, 0.5])
+    omega, resid, Xn = krylov.rayleigh_residual(op, X)
+    assert np.allclose(np.linalg.norm(Xn, axis=0), 1.0, atol=1e-14)
+    for i in range(X.shape[1]):
+        x = X[:, i] / np.linalg.norm(X[:, i])
+        w = np.vdot(x, op.apply_u(x))
+        assert abs(omega[i] - w) < 1e-14
+        assert abs(omega[i]) < 0.5                        # random vectors: far from the circle
+        assert abs(resid[i] ** 2 - (1.0 - abs(omega[i]) ** 2)) < 1e-13
+    # and on a mixture of two exact eigenvectors with weights (a, b): omega = a^2 l1 + b^2 l2,
+    # residual^2 = a^2 b^2 |l1 - l2|^2
+    w_all, V = np.linalg.eig(op.dense())
+    a, b = 0.8, 0.6
+    x = a * V[:, 3] / np.linalg.norm(V[:, 3]) + b * V[:, 7] / np.linalg.norm(V[:, 7])
+    om2, r2, _ = krylov.rayleigh_residual(op, x[:, None])
+    assert abs(om2[0] - (a * a * w_all[3] + b * b * w_all[7])) < 1e-12
+    assert abs(r2[0] ** 2 - (a * b * abs(w_all[3] - w_all[7])) ** 2) < 1e-12
+
+
 def test_select_closest_brute_force():
     rng = np.random.default_rng(21)
     ang = rng.uniform(-math.pi, math.pi, 50)
