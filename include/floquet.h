@@ -146,6 +146,16 @@ int filter_apply(floquet_t op, double phi, int64_t k, const void* psi_in, void* 
 int floquet_polish_correction(floquet_t op, double phi, int64_t K, const double* omega,
                               const void* R, void* out, int n, int sweep, void* stream);
 
+/* Host-only query of the U application's pass plan (no GPU needed): the passes that split
+ * the L qubits' X kicks (Sec. 2, matrix-free product) for tiles of 2^NB amplitudes whose later
+ * passes keep at least min_cols contiguous low bits. For pass i, out[6i .. 6i+5] =
+ * (NB, c, start, kick_from, midbits, topshift): the tile holds global bits [0, c) and
+ * [start, start + NB - c), the pass kicks tile bits [kick_from, NB), and the kernels place
+ * tile bits at c.. with the shifts midbits = start - c and topshift = start + NB - c (0 and L
+ * for a single pass). *n_passes receives the count; EINVAL for L outside [1, 30], NB < 1,
+ * min_cols outside [0, NB), NULL pointers or fewer than *n_passes slots. */
+int floquet_pass_plan(int L, int NB, int min_cols, int* out, int max_passes, int* n_passes);
+
 /* One classical Gram-Schmidt step with one full reorthogonalisation (CGS2) of Sec. 4's
  * Arnoldi process: w <- (w - V V^H w) / beta, twice projected, for n >= 0 orthonormal
  * columns V (device, d x n complex128, column-major, leading dimension d).

@@ -262,6 +262,42 @@ static Plan make_plan(int L, int NBmax, int min_cols) {
   return p;
 }
 
+}  // namespace fq
+
+// Host-only query of the pass plan (C ABI): the passes make_plan forms and the two derived
+// index fields the kernels receive (midbits = start - c, topshift = start + NB - c; for a
+// single pass 0 and L).
+extern "C" int floquet_pass_plan(int L, int NB, int min_cols, int* out, int max_passes,
+                                 int* n_passes) {
+  using namespace fq;
+  if (L < 1 || L > 30 || NB < 1 || min_cols < 0 || min_cols >= NB || !out || !n_passes ||
+      max_passes < 1) {
+    set_error("floquet_pass_plan: invalid arguments");
+    return FLOQUET_EINVAL;
+  }
+  const Plan p = make_plan(L, NB, min_cols);
+  *n_passes = (int)p.passes.size();
+  if ((int)p.passes.size() > max_passes) {
+    set_error("floquet_pass_plan: %d passes, room for %d", (int)p.passes.size(), max_passes);
+    return FLOQUET_EINVAL;
+  }
+  for (size_t i = 0; i < p.passes.size(); ++i) {
+    const Pass& ps = p.passes[i];
+    const bool single = ps.NB == L;
+    int* o = out + 6 * i;
+    o[0] = ps.NB;
+    o[1] = ps.c;
+    o[2] = ps.start;
+    o[3] = ps.kick_from;
+    o[4] = single ? 0 : ps.start - ps.c;
+    o[5] = single ? L : ps.start + ps.NB - ps.c;
+  }
+  set_error("%s", "");
+  return FLOQUET_OK;
+}
+
+namespace fq {
+
 template <typename Real>
 static PassArgs<Real> make_args(const floquet_op* op, const Pass& ps, const cplx<Real>* tlo,
                                 const cplx<Real>* thi) {

@@ -36,6 +36,8 @@ SIGNATURES = {
     "filter_apply": (_c_int, [_c_void_p, _c_double, _c_int64, _c_void_p, _c_void_p, _c_int,
                               _c_int, _c_int, _c_void_p]),
     "gram_schmidt": (_c_int, [_c_int64, _c_void_p, _c_int, _c_void_p, _dptr, _c_void_p]),
+    "floquet_pass_plan": (_c_int, [_c_int, _c_int, _c_int, ctypes.POINTER(_c_int), _c_int,
+                                   ctypes.POINTER(_c_int)]),
     "floquet_polish_correction": (_c_int, [_c_void_p, _c_double, _c_int64, _dptr, _c_void_p,
                                            _c_void_p, _c_int, _c_int, _c_void_p]),
     "gram_schmidt_noalloc": (_c_int, [_c_int64, _c_void_p, _c_int, _c_void_p, _c_void_p,
@@ -239,6 +241,15 @@ class Floquet:
         if check and rc not in (OK, ENOCONV):
             raise FloquetError(rc, "arnoldi_eigs")
         return ev[0::2] + 1j * ev[1::2], res, nconv.value, rc
+
+
+def pass_plan(L, NB, min_cols):
+    """The U application's pass plan: a list of (NB, c, start, kick_from, midbits, topshift)."""
+    out = (_c_int * (6 * 64))()
+    n = _c_int()
+    _check(lib().floquet_pass_plan(int(L), int(NB), int(min_cols), out, 64, ctypes.byref(n)),
+           "floquet_pass_plan")
+    return [tuple(out[6 * i: 6 * i + 6]) for i in range(n.value)]
 
 
 def gram_schmidt(V, n, w, stream=None):

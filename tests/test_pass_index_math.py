@@ -139,3 +139,22 @@ def test_pipelined_rounds_kick_tile_bits_once(nb, RB, kf):
     his = [nb] + gs[:-1]
     kicked = [g + b for g, h in zip(gs, his) for b in range(RB) if kf <= g + b < h]
     assert sorted(kicked) == list(range(kf, nb))
+
+
+def test_library_plan_matches_the_derivation():
+    # the plan and the derived index shifts the library itself uses (host-only C-ABI query),
+    # against the derivation above: a change to the C++ plan fails here
+    from paper_2102_05054_gb300 import build, floquet
+    build.build()
+    for L in range(3, 25):
+        for nb, cols in [(9, 3), (10, 3), (10, 4), (11, 2), (11, 3), (11, 4), (12, 3), (12, 4)]:
+            got = floquet.pass_plan(L, nb, cols)
+            want = make_plan(L, nb, cols)
+            assert [g[:4] for g in got] == [tuple(w) for w in want], (L, nb, cols)
+            for (b, c, start, kf, mid, top) in got:
+                if b == L:
+                    assert (mid, top) == (0, L)
+                else:
+                    assert (mid, top) == (start - c, start + b - c)
+    with pytest.raises(RuntimeError):
+        floquet.pass_plan(20, 11, 11)   # min_cols must leave qubits to kick
