@@ -330,12 +330,4 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
                   int64_t out_stride, const cplx<Real>* zs, int64_t k, int nvec,
                   int vec_per_prob, bool use_graph, cudaStream_t st);
 
-// General Horner evaluation out_v = sum_{l=0}^{k-1} c_l (z_v U)^l in_v with c_{k-1} = 1 and
-// the other coefficients c_l = hcoef[k-1-l] (hcoef: device, k complex of Real, shared by the
-// vectors; hcoef[0] is not read): acc <- in, then acc <- hcoef[j] in + z U acc, j = 1..k-1.
-template <typename Real, typename Rio>
-int filter_horner_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio>* out,
-                       int64_t out_stride, const cplx<Real>* zs, const cplx<Real>* hcoef,
-                       int64_t k, int nvec, cudaStream_t st);
-
 }  // namespace fq

@@ -453,12 +453,12 @@ static int launch_horner_grid_shape(const HornerGridArgs<Real>& a, bool swap, bo
     set_error("horner_grid: shape (NB %d, C %d) does not fit L = %d", NB, C, a.L);
     return FLOQUET_EINVAL;
   }
-  switch ((swap ? 2 : 0) + (gen ? 1 : 0)) {
-    case 0: return launch_horner_grid_t<Real, NB, RB, C, false, false>(a, st);
-    case 1: return launch_horner_grid_t<Real, NB, RB, C, false, true>(a, st);
-    case 2: return launch_horner_grid_t<Real, NB, RB, C, true, false>(a, st);
-    default: return launch_horner_grid_t<Real, NB, RB, C, true, true>(a, st);
+  if (gen) {  // per-step coefficients: not compiled into the launchers (no caller uses them)
+    set_error("horner_grid: general Horner coefficients are not compiled in");
+    return FLOQUET_EINVAL;
   }
+  return swap ? launch_horner_grid_t<Real, NB, RB, C, true, false>(a, st)
+              : launch_horner_grid_t<Real, NB, RB, C, false, false>(a, st);
 }
 
 // Launchers of the persistent Horner kernel for chains of L qubits in sweep precision Real,

@@ -1018,79 +1018,6 @@ int filter_horner(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<R
   return launch_convert_strided<Real, Rio>(acc, out, out_stride, d, nvec, st);
 }
 
-template <typename Real, typename Rio>
-int filter_horner_coef(floquet_op* op, const cplx<Rio>* in, int64_t in_stride, cplx<Rio>* out,
-                       int64_t out_stride, const cplx<Real>* zs, const cplx<Real>* hcoef,
-                       int64_t k, int nvec, cudaStream_t st) {
-  using C = cplx<Real>;
-  const int64_t d = op->d;
-  if (op->brick) {
-    set_error("general Horner filter: kicked-Ising operators only");
-    return FLOQUET_EINVAL;
-  }
-  FQ_TRY(tune<Real>(op, nvec, st));
-  FQ_TRY(ensure_workspace(op, (size_t)nvec * d * sizeof(C)));
-  C* pin = reinterpret_cast<C*>(op->psi_in_copy);
-  C* acc = reinterpret_cast<C*>(op->acc);
-  const int64_t lo_n = op->tabs.lo_n;
-  const size_t zbytes = (size_t)nvec * lo_n * sizeof(C);
-  if (op->zlo_bytes < zbytes) {
-    destroy_graphs(op);
-    cudaFree(op->zlo);
-    op->zlo = nullptr;
-    op->zlo_bytes = 0;
-    if (cudaMalloc(&op->zlo, zbytes) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("filter workspace: cudaMalloc of %zu bytes failed", zbytes);
-      return FLOQUET_ENOMEM;
-    }
-    op->zlo_bytes = zbytes;
-  }
-  C* zlo = reinterpret_cast<C*>(op->zlo);
-  scale_lo_kernel<Real><<<grid_for(nvec * lo_n, 256), 256, 0, st>>>(
-      tlo_of<Real>(op), lo_n, nvec, zs, zlo, nvec * lo_n);
-  count_launch();
-  FQ_CHECK_LAUNCH();
-  FQ_TRY((launch_filter_init<Rio, Real>(in, in_stride, nullptr, pin, nullptr, 0, d, nvec, st)));
-  if (k > 1) {
-    const int gsi = op->gshape[sweep_dtype<Real>()];
-    const std::vector<HornerGridShape<Real>> gshapes = horner_grid_shapes<Real>(op->L);
-    if (gsi >= 0 && gsi < (int)gshapes.size()) {
-      FQ_TRY(ensure_bar(op));
-      HornerGridArgs<Real> ga = grid_args<Real>(op, pin, acc, zlo, lo_n, k, nvec, nvec);
-      ga.coef = hcoef;
-      ga.coef_stride = 0;
-      const HornerGridLaunch<Real> gl = gshapes[gsi].launch;
-      auto gbody = [&](cudaStream_t s) -> int { return gl(ga, op->swap, true, s); };
-      FQ_TRY(run_loop(op, false, k, nvec, sweep_dtype<Real>(), FLOQUET_FORM_HORNER, hcoef,
-                      nvec, 1, st, gbody));
-    } else {
-      FQ_CUDA(cudaMemcpyAsync(acc, pin, sizeof(C) * nvec * d, cudaMemcpyDeviceToDevice, st));
-      auto body = [&](cudaStream_t s) -> int {
-        for (int64_t j = 1; j < k; ++j)
-          FQ_TRY(u_passes<Real>(op, acc, acc, nvec, nvec, EPI_PHASE_HORNER, nullptr, nullptr, 0,
-                                (int)j, pin, s, zlo, hcoef, 0));
-        return FLOQUET_OK;
-      };
-      FQ_TRY(run_loop(op, false, k, nvec, sweep_dtype<Real>(), FLOQUET_FORM_HORNER, hcoef,
-                      nvec, 0, st, body));
-    }
-  } else {
-    FQ_CUDA(cudaMemcpyAsync(acc, pin, sizeof(C) * nvec * d, cudaMemcpyDeviceToDevice, st));
-  }
-  return launch_convert_strided<Real, Rio>(acc, out, out_stride, d, nvec, st);
-}
-
-template int filter_horner_coef<float, double>(floquet_op*, const double2*, int64_t, double2*,
-                                               int64_t, const float2*, const float2*, int64_t,
-                                               int, cudaStream_t);
-template int filter_horner_coef<dfloat, double>(floquet_op*, const double2*, int64_t, double2*,
-                                                int64_t, const float4*, const float4*, int64_t,
-                                                int, cudaStream_t);
-template int filter_horner_coef<double, double>(floquet_op*, const double2*, int64_t, double2*,
-                                                int64_t, const double2*, const double2*,
-                                                int64_t, int, cudaStream_t);
-
 #define FQ_INST_FILTER(R, RIO)                                                            \
   template int filter_coef<R, RIO>(floquet_op*, const cplx<RIO>*, int64_t, cplx<RIO>*, int64_t, \
                                    const cplx<R>*, int64_t, int, int, bool, cudaStream_t);      \
