@@ -75,3 +75,28 @@ def test_reference_arm_non_zero_ranks_exit_quietly():
     r = _run_bench({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
     assert r.returncode == 0
     assert not [line for line in r.stdout.splitlines() if line.startswith("{")]
+
+
+def test_step_seeds_and_batches():
+    sys.path.insert(0, ROOT)
+    import bench
+    # K steps of rank r solve realisations base + r K + i: distinct within and across ranks
+    s0 = bench.step_seeds(1, 0, 20)
+    s1 = bench.step_seeds(1, 1, 20)
+    assert s0 == list(range(1, 21)) and s1 == list(range(21, 41))
+    assert not set(s0) & set(s1)
+    # lockstep solves cover every step exactly once, at most `batch` at a time
+    for steps, batch in [(20, 2), (7, 2), (5, 4), (1, 2), (3, 1)]:
+        b = bench.batches(steps, batch)
+        assert sum(b) == steps and max(b) <= batch and min(b) >= 1
+    assert bench.batches(0, 2) == []
+
+
+def test_df_instruction_count_is_the_algorithmic_formula():
+    sys.path.insert(0, ROOT)
+    import bench
+    # two real outputs per amplitude per kicked qubit, 12 FP32 instructions each; one
+    # double-float complex product (44) and one complex multiply-add (60) for the Horner
+    # epilogue, a second product (44) for the accumulate form
+    assert bench.df_instr_per_amplitude(20, "horner") == 24 * 20 + 44 + 60 == 584
+    assert bench.df_instr_per_amplitude(16, "acc") == 24 * 16 + 44 + 44 + 60
