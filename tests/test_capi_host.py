@@ -99,3 +99,21 @@ def test_suggest_params_matches_oracle(lib):
                     continue
                 assert floquet.suggest_params(L, nev, max_m) == want, (L, nev, max_m)
     assert lib.floquet_suggest_params(2, 1, 512, None, None) == floquet.EINVAL
+
+
+def test_create_without_a_usable_device_fails_cleanly(lib):
+    # failure detection on the host: with no usable CUDA device (this CPU container) the
+    # device allocation inside floquet_create fails; the call must return FLOQUET_ECUDA, leave
+    # the handle NULL, name the failing call in the thread's error message, and leave the
+    # library usable (a host-only query still works)
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present: the allocation does not fail")
+    from paper_2102_05054_gb300 import floquet
+    h = np.zeros(8)
+    handle = ctypes.c_void_p()
+    rc = lib.floquet_create(8, 1.0, 0.9, h.ctypes.data_as(floquet._dptr), ctypes.byref(handle))
+    assert rc == floquet.ECUDA
+    assert handle.value is None
+    assert b"cudaMalloc" in lib.floquet_last_error()
+    assert floquet.pass_plan(20, 11, 2)[0][:4] == (11, 11, 11, 0)
