@@ -4,6 +4,7 @@ function include/floquet.h declares, and rejects invalid arguments before touchi
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -117,3 +118,17 @@ def test_create_without_a_usable_device_fails_cleanly(lib):
     assert handle.value is None
     assert b"cudaMalloc" in lib.floquet_last_error()
     assert floquet.pass_plan(20, 11, 2)[0][:4] == (11, 11, 11, 0)
+
+
+def test_header_compiles_as_c99_and_cxx(tmp_path):
+    # the boundary is a C ABI: the public header must be valid C as well as C++
+    import shutil
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "floquet.h"\nint main(void) { return 0; }\n')
+    inc = os.path.join(ROOT, "include")
+    for cc, flags in [("gcc", ["-std=c99"]), ("g++", ["-std=c++17", "-x", "c++"])]:
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not found")
+        r = subprocess.run([cc, *flags, "-Wall", "-Werror", "-I", inc, "-c", str(src), "-o",
+                            str(tmp_path / "out.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
