@@ -449,6 +449,63 @@ def u_timing(Ls, nvecs=(1, 2, 4), k=513, reps=3):
                       flush=True)
 
 
+def km_grid(L, nev, k0, m0, max_m=512):
+    """(k, m) points of the parameter scan (the paper's Fig. bench scans the filter length and
+    the Krylov dimension): k in k0 x {1/4, 1/2, 1, 2} (at least 2, at most d / 2) and m in
+    m0 x {0.75, 1, 1.5, 2} (at least nev + 16, the room a convergence check needs, at most
+    min(max_m, d - 1)); duplicates removed, sorted."""
+    d = 1 << L
+    ks = sorted({int(min(max(2, round(k0 * f)), d // 2)) for f in (0.25, 0.5, 1.0, 2.0)})
+    ms = sorted({int(min(max(nev + 16, round(m0 * f)), max_m, d - 1))
+                 for f in (0.75, 1.0, 1.5, 2.0)})
+    return [(k, m) for k in ks for m in ms if m > nev]
+
+
+def km_scan(args):
+    """Time to the workload's nev pairs (every residual <= 1e-10) for each (k, m) of
+    km_grid around the workload's own pair, plus the paper's rule (suggest_params): one JSON
+    line per point (CUDA events around one solve; U applications from the library's
+    profiling hook), then the fastest point."""
+    import torch
+
+    from paper_2102_05054_gb300 import floquet, inputs
+    cfg = _cfg(args)
+    L, nev, phi = cfg["L"], cfg["nev"], cfg["phi"]
+    prec = {"fp64": floquet.FP64, "filter_df": floquet.FILTER_DF}[cfg["precision"]]
+    kind = {floquet.FP64: "c128", floquet.FILTER_DF: "df"}[prec]
+    pts = km_grid(L, nev, cfg["k"], cfg["m"])
+    rule = floquet.suggest_params(L, nev)
+    if rule not in pts:
+        pts.append(rule)
+    h = inputs.disorder(L, cfg["W"], cfg["seed"])
+    v0 = torch.from_numpy(inputs.start_vector(L)).cuda()
+    stream = torch.cuda.current_stream()
+    best = None
+    for (k, m) in pts:
+        with floquet.Floquet(L, inputs.J_DEFAULT, inputs.G_DEFAULT, h) as fq:
+            floquet.profile_enable(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            om, res, nconv, rc = fq.arnoldi_eigs(phi, k, nev, m, v0, tol=args.tol,
+                                                 precision=prec,
+                                                 max_restarts=args.max_restarts, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof = floquet.profile_read()
+            floquet.profile_enable(False)
+        t = e0.elapsed_time(e1) / 1000.0
+        ok = rc == floquet.OK and nconv == nev and float(np.max(res)) <= 1e-10
+        line = {"L": L, "nev": nev, "k": k, "m": m, "paper_rule": (k, m) == rule,
+                "seconds": round(t, 3), "status": int(rc), "n_conv": int(nconv),
+                "max_resid": float(np.max(res)) if len(res) else None,
+                "u_applications": int(prof[kind][1]), "precision": cfg["precision"]}
+        print(json.dumps(line), flush=True)
+        if ok and (best is None or t < best["seconds"]):
+            best = line
+    print(json.dumps({"fastest": best, "paper_rule": list(rule)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,12 +523,18 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--km-scan", action="store_true",
+                    help="time the workload's solve over a (k, m) grid around its own pair and "
+                         "the paper's rule instead of the benchmark line")
     ap.add_argument("--u-timing", default=None,
                     help="comma-separated L values: print per-U-application filter times per "
                          "sweep precision instead of the benchmark line")
     args = ap.parse_args()
     if args.u_timing:
         u_timing([int(x) for x in args.u_timing.split(",")])
+        return
+    if args.km_scan:
+        km_scan(args)
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -100,3 +100,17 @@ def test_df_instruction_count_is_the_algorithmic_formula():
     # epilogue, a second product (44) for the accumulate form
     assert bench.df_instr_per_amplitude(20, "horner") == 24 * 20 + 44 + 60 == 584
     assert bench.df_instr_per_amplitude(16, "acc") == 24 * 16 + 44 + 44 + 60
+
+
+def test_km_grid_points_are_feasible():
+    sys.path.insert(0, ROOT)
+    import bench
+    for L, nev, k0, m0 in [(20, 100, 16384, 256), (16, 50, 1024, 160), (10, 10, 64, 64),
+                           (12, 16, 256, 64)]:
+        pts = bench.km_grid(L, nev, k0, m0)
+        assert (k0, m0) in pts
+        assert len(pts) == len(set(pts))
+        for k, m in pts:
+            assert 2 <= k <= (1 << L) // 2
+            assert nev < m <= min(512, (1 << L) - 1)
+            assert m >= min(nev + 16, (1 << L) - 1)
