@@ -14,7 +14,8 @@ Readings taken where the paper is silent:
   * the eigenvalue is the Rayleigh quotient itself, not projected onto |omega| = 1;
   * Gram-Schmidt is classical with one full reorthogonalisation (CGS2).
 
-Parity: ``arnoldi`` is pinned by V^H V = I and g_k(U) V_m = V_{m+1} H_m; ``dense_eigs`` by
+Parity: ``arnoldi`` is pinned by V^H V = I and g_k(U) V_m = V_{m+1} H_m; ``block_arnoldi``
+by its b = 1 case, the block relation and exact eigenvalues on the whole space; ``dense_eigs`` by
 unitarity and the closed-form spectra of the special cases; ``arpack_eigs`` against
 ``dense_eigs`` (tests/test_oracle.py).
 """
@@ -51,6 +52,40 @@ def arnoldi(apply_op, v0, m):
         H[: j + 1, j] = h
         H[j + 1, j] = beta
         V[:, j + 1] = q
+    return V, H
+
+
+def block_arnoldi(apply_block, V0, nblocks):
+    """Block Arnoldi with b = V0.shape[1] start vectors: the block Krylov space
+    span{V0, A V0, ..., A^nblocks V0} of the operator A (apply_block maps a d x b block to
+    A times it), the multi-vector extension of Eq. arnoldi that a filter applied to b vectors
+    per launch serves. Column by column: each new vector A v_i is orthogonalised against every
+    earlier column by CGS2 (``cgs2``). Returns V (d x (nblocks+1) b, orthonormal) and H
+    ((nblocks+1) b x nblocks b, zero below its b-th subdiagonal) with
+    apply_block(V[:, :nblocks b]) = V @ H. Assumes no breakdown (random start blocks).
+
+    Parity: pinned by the b = 1 case (identical to ``arnoldi``), V^H V = I, the block
+    relation, the band structure, and exact eigenvalues once the space is the whole space
+    (tests/test_oracle.py)."""
+    d, b = V0.shape
+    n = (nblocks + 1) * b
+    V = np.zeros((d, n), dtype=np.complex128)
+    H = np.zeros((n, nblocks * b), dtype=np.complex128)
+    # orthonormal start block (CGS2 column by column)
+    for i in range(b):
+        if i == 0:
+            V[:, 0] = V0[:, 0] / np.linalg.norm(V0[:, 0])
+        else:
+            _, _, V[:, i] = cgs2(V[:, :i], V0[:, i])
+    for j in range(nblocks):
+        W = apply_block(V[:, j * b:(j + 1) * b])
+        for i in range(b):
+            col = j * b + i            # column of H: A v_col
+            new = (j + 1) * b + i      # index of the vector it produces
+            h, beta, q = cgs2(V[:, :new], W[:, i])
+            H[:new, col] = h
+            H[new, col] = beta
+            V[:, new] = q
     return V, H
 
 

@@ -582,3 +582,53 @@ def test_defect_coefficients_identity():
             rhs += coef * p
             p = U @ p
         assert np.linalg.norm(lhs - rhs) < 1e-12 * np.linalg.norm(lhs)
+
+
+def test_block_arnoldi_reduces_to_arnoldi_and_keeps_its_relation():
+    L = 8
+    op = model.KickedIsing(L, 1.0, 0.9045, inputs.disorder(L, 1.0, 31))
+    d = 1 << L
+    # b = 1: the same basis and Hessenberg matrix as the single-vector Arnoldi
+    v0 = inputs.complex_gaussian(d, 5)
+    V1, H1 = krylov.arnoldi(op.apply_u, v0, 12)
+    Vb, Hb = krylov.block_arnoldi(op.apply_u_block, v0[:, None], 12)
+    assert np.abs(V1 - Vb).max() < 1e-12 and np.abs(H1 - Hb).max() < 1e-12
+    # b = 3 on g_k(U): orthonormal basis, A V_n = V H, band structure below the b-th diagonal
+    b, nb = 3, 7
+    V0 = inputs.random_states(d, b, 6)
+    apply_g = lambda X: np.stack([geosum.filter_acc(op, X[:, i], 0.4, 9)
+                                  for i in range(X.shape[1])], axis=1)
+    V, H = krylov.block_arnoldi(apply_g, V0, nb)
+    assert np.abs(V.conj().T @ V - np.eye(V.shape[1])).max() < 1e-12
+    assert np.abs(apply_g(V[:, :nb * b]) - V @ H).max() < 1e-11 * np.abs(H).max()
+    rows, cols = np.nonzero(np.abs(H) > 0)
+    assert np.all(rows <= cols + b)
+    # the start block lies in the space (its columns are combinations of the first b)
+    P = V[:, :b] @ (V[:, :b].conj().T @ V0)
+    assert np.abs(P - V0).max() < 1e-12
+
+
+def test_block_arnoldi_spans_the_block_krylov_space():
+    # span V[:, :(j+1) b] = span{V0, U V0, ..., U^j V0} (the definition of the space), checked
+    # against the explicit power basis; and with d = (nblocks + 1) b the basis is all of C^d,
+    # so V^H U V has U's eigenvalues, its first nblocks b columns being H
+    L = 6
+    op = model.KickedIsing(L, 0.8, 0.6, inputs.disorder(L, 1.0, 32))
+    d, b, nb = 1 << L, 3, 4
+    V0 = inputs.random_states(d, b, 7)
+    V, H = krylov.block_arnoldi(op.apply_u_block, V0, nb)
+    K = V0.copy()
+    P = V0.copy()
+    for j in range(nb + 1):
+        Q = V[:, :(j + 1) * b]
+        assert np.abs(K - Q @ (Q.conj().T @ K)).max() < 1e-10 * np.abs(K).max(), j
+        P = op.apply_u_block(P)
+        K = np.concatenate([K, P], axis=1)
+    L2 = 4
+    op2 = model.KickedIsing(L2, 0.8, 0.6, inputs.disorder(L2, 1.0, 33))
+    V2, H2 = krylov.block_arnoldi(op2.apply_u_block, inputs.random_states(16, 4, 8), 3)
+    G = V2.conj().T @ op2.apply_u_block(V2)
+    assert np.abs(G[:, :12] - H2).max() < 1e-12
+    lam = np.linalg.eigvals(G)
+    want = np.linalg.eigvals(op2.dense())
+    assert np.abs(np.sort_complex(lam)[:, None] - want[None, :]).min(axis=1).max() < 1e-11
