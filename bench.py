@@ -521,7 +521,7 @@ def main():
                          "<= 1e-10 of every returned pair is checked separately)")
     ap.add_argument("--max-restarts", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--km-scan", action="store_true",
                     help="time the workload's solve over a (k, m) grid around its own pair and "
